@@ -1,0 +1,186 @@
+/*
+ * ls.h -- C ABI of libls, the GB300 (sm_103a) implementation of the Li & Stephens all-vs-all
+ * hot path of the kalis paper (arXiv 2212.11403): forward and backward recursions over N
+ * independent copying HMMs, posterior decoding and the local distance matrix.
+ *
+ * Conventions shared by every call
+ *   - Loci are 0-based (the paper's variant l is locus l-1 here); haplotypes (recipients i,
+ *     donors j) are 0-based.
+ *   - Matrices are recipient-major: X[i*N + j] holds the paper's X_ji (the paper's column i,
+ *     Sec. 2.1, stored contiguously).  A table over targets [t_from, t_to) stores row r for
+ *     target t_from + r.
+ *   - rho[l], l = 0..L-2, is the recombination probability of the interval between loci l and
+ *     l+1; the forward step l -> l+1 and the backward step l+1 -> l both use it.
+ *   - Pointers documented "device" must be CUDA device memory (e.g. a torch tensor's
+ *     data_ptr()); "host" pointers are ordinary CPU memory.  The caller owns every pointer it
+ *     passes; contexts and tables are owned by the library and freed by the matching destroy.
+ *   - Every call that takes a stream enqueues its work on that stream (a cudaStream_t passed as
+ *     ls_stream_t; NULL = the legacy default stream) and returns without waiting, unless stated.
+ *   - Return value: LS_OK (0), a positive warning, or a negative error; on error nothing was
+ *     enqueued and ls_last_error() (per calling thread) describes the cause.
+ *   - Floating point: recurrences in FP32, per-target log scales in FP64.
+ */
+#ifndef LS_H
+#define LS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------------------------- */
+#define LS_OK 0
+#define LS_WARN_UNDERFLOW 1      /* some target hit total underflow (App. A.3); see status_out */
+#define LS_WARN_OVERFLOW 2       /* some target hit total overflow (App. A.3); see status_out  */
+#define LS_ERR_ARG (-1)          /* bad argument (null pointer, size, range, invalid prior)     */
+#define LS_ERR_PARAM_MISMATCH (-2) /* table propagated under another parameter set (Sec. 4.1.2) */
+#define LS_ERR_DIRECTION (-3)    /* forward asked to move to an earlier locus, backward to later */
+#define LS_ERR_LOCUS_MISMATCH (-4) /* forward and backward tables are not at the same locus     */
+#define LS_ERR_RANGE (-5)        /* tables cover different targets / distance needs all targets */
+#define LS_ERR_CUDA (-6)         /* a CUDA runtime call failed                                   */
+#define LS_ERR_OOM (-7)          /* device memory allocation failed                              */
+#define LS_ERR_STATE (-8)        /* parameters not set, or table not initialised                */
+#define LS_ERR_DEVICE (-9)       /* a device-side wait ran out its time limit                    */
+#define LS_ERR_UNSUPPORTED (-10) /* size or option outside what this build supports              */
+
+/* per-target status bits written to status_out arrays */
+#define LS_STATUS_UNDERFLOW 1u   /* a normaliser sum was 0 or subnormal                          */
+#define LS_STATUS_OVERFLOW 2u    /* a normaliser sum was not finite                              */
+#define LS_STATUS_TIMEOUT 4u     /* a device wait for staged haplotype rows ran out              */
+
+#define LS_FWD 0
+#define LS_BWD 1
+
+typedef void* ls_stream_t; /* a cudaStream_t */
+typedef struct ls_ctx ls_ctx;
+typedef struct ls_table ls_table;
+
+/* Library version and build description (arch, kernel variants).  Static string. */
+const char* ls_version(void);
+
+/* Text of the last error raised on the calling thread ("" if none).  Thread-local storage. */
+const char* ls_last_error(void);
+
+/* ---- haplotype cache (Sec. 3.2, Sec. 4.1.1: CacheHaplotypes / QueryCache / CacheSummary) --- */
+
+/* Create a context holding one haplotype data set on the current CUDA device.
+ * haps: host uint8 [L][N], variant-major, entries 0/1 (the paper's L x N matrix h, Sec. 2.1).
+ * The data are packed on the device into variant-major rows of 32 haplotypes per uint32
+ * (haplotype i in bit i%32 of word i/32, Sec. 4.1.1), each row padded to a 16-byte multiple with
+ * at least one zero word.  Synchronous.  N >= 2, L >= 1.  *out receives the context. */
+int ls_create(ls_ctx** out, const uint8_t* haps, int32_t N, int32_t L);
+
+/* Same, from haplotypes already packed on the device: packed [L][row_words] uint32 in the layout
+ * above (row_words >= ceil(N/32)); bits beyond N are ignored.  The data are copied.  Synchronous. */
+int ls_create_packed(ls_ctx** out, const uint32_t* packed, int32_t N, int32_t L, int32_t row_words);
+
+/* Free a context and everything it owns (tables created from it must be destroyed first). */
+int ls_destroy(ls_ctx* ctx);
+
+/* N, L, words per packed row, and device bytes held by the context (any pointer may be NULL). */
+int ls_info(const ls_ctx* ctx, int32_t* N, int32_t* L, int32_t* row_words, size_t* device_bytes);
+
+/* Read haplotypes back from the packed cache: out[a*nh + b] = h at locus loci[a], haplotype
+ * haps[b].  All arrays host.  Synchronous. */
+int ls_query(const ls_ctx* ctx, const int32_t* loci, int32_t nl, const int32_t* haps, int32_t nh, uint8_t* out);
+
+/* Copy the packed cache to host memory out [L][row_words].  Synchronous. */
+int ls_export_packed(const ls_ctx* ctx, uint32_t* out);
+
+/* ---- parameters (Sec. 3.3 Parameters / CalcRho; Sec. 4.1.2) ---------------------------------- */
+
+/* Eq. rho: rho_out[k] = 1 - exp(-Ne * m[k]^gamma), evaluated as -expm1(.).  m in Morgans.
+ * Host arrays.  Errors on n < 0, a negative or non-finite m, Ne < 0 or gamma <= 0. */
+int ls_calc_rho(const double* m, int32_t n, double Ne, double gamma, double* rho_out);
+
+/* Set the model parameters of a context (Sec. 2.1): rho host double [L-1] with 0 <= rho <= 1;
+ * mu host double [mu_len], mu_len 1 (scalar) or L, 0 <= mu <= 1/2; Pi NULL for the uniform
+ * prior 1/(N-1), otherwise device float [N][N] recipient-major (Pi[i*N+j] = prior that recipient
+ * i copies donor j) with a zero diagonal and rows summing to 1 within 1e-5 (copied).
+ * Tables propagated under an earlier parameter set are refused afterwards
+ * (LS_ERR_PARAM_MISMATCH).  *hash_out (may be NULL) receives the parameter fingerprint.
+ * Synchronous. */
+int ls_set_params(ls_ctx* ctx, const double* rho, const double* mu, int32_t mu_len, const float* Pi,
+                  uint64_t* hash_out);
+
+/* ---- forward / backward tables (Sec. 3.4-3.5, Table tab:fwdbck) ----------------------------- */
+
+/* Create a table (kind LS_FWD or LS_BWD) for targets [t_from, t_to), 0 <= t_from < t_to <= N.
+ * The table is uninitialised (no locus): the first ls_forward initialises it at locus 0, the
+ * first ls_backward at locus L-1 (Sec. 3.5).  Device memory: (t_to-t_from) * N floats plus one
+ * double per target.  Requires parameters to be set. */
+int ls_table_create(ls_ctx* ctx, int32_t kind, int32_t t_from, int32_t t_to, ls_table** out);
+
+/* Free a table. */
+int ls_table_destroy(ls_table* t);
+
+/* CopyTable: deep copy src into dst (same kind and target range).  Enqueued on stream. */
+int ls_table_copy(ls_table* dst, const ls_table* src, ls_stream_t stream);
+
+/* ResetTable: mark the table uninitialised again (no device work). */
+int ls_table_reset(ls_table* t);
+
+/* kind, current locus (-1 if uninitialised), target range and parameter fingerprint. */
+int ls_table_info(const ls_table* t, int32_t* kind, int32_t* locus, int32_t* t_from, int32_t* t_to,
+                  uint64_t* hash);
+
+/* Copy the table's contents to caller device memory: state [T][N] floats (forward: alpha of
+ * Eq. fwd1; backward: beta of Eq. bck1, i.e. beta not pre-multiplied by theta) and logscale [T]
+ * doubles (forward: log F at the current locus, Eq. F; backward: log G at the current locus,
+ * Eq. G, with G = 1 at the last locus).  Either pointer may be NULL.  Enqueued on stream. */
+int ls_table_read(const ls_table* t, float* state, double* logscale, ls_stream_t stream);
+
+/* Forward (Eq. fwd0, fwd1): propagate fwd in place to locus to_locus >= its current locus
+ * (an uninitialised table starts at locus 0).  If n_store > 0, alpha at each locus in
+ * store_loci (host int32, strictly increasing, within (current, to_locus]) is written to
+ * alpha_out (device float [n_store][T][N]).  status_out (device uint32 [T], may be NULL) is
+ * OR-ed with per-target LS_STATUS_* bits.  Errors: LS_ERR_DIRECTION, LS_ERR_PARAM_MISMATCH. */
+int ls_forward(ls_ctx* ctx, ls_table* fwd, int32_t to_locus, const int32_t* store_loci, int32_t n_store,
+               float* alpha_out, uint32_t* status_out, ls_stream_t stream);
+
+/* Backward (Eq. bck0, bck1): propagate bck in place to locus to_locus <= its current locus
+ * (an uninitialised table starts at locus L-1).  store_loci strictly decreasing within
+ * [to_locus, current); beta at those loci goes to beta_out [n_store][T][N].  Otherwise as
+ * ls_forward. */
+int ls_backward(ls_ctx* ctx, ls_table* bck, int32_t to_locus, const int32_t* store_loci, int32_t n_store,
+                float* beta_out, uint32_t* status_out, ls_stream_t stream);
+
+/* PostProbs (Eq. postprob): p_out device float [T][N], p_out[r*N+j] = posterior that target
+ * t_from+r copies donor j; p = epsilon (DBL_EPSILON) for every donor if the normaliser is 0;
+ * the diagonal is 0.  Both tables must cover the same targets and sit at the same locus
+ * (LS_ERR_RANGE / LS_ERR_LOCUS_MISMATCH). */
+int ls_posterior(ls_ctx* ctx, const ls_table* fwd, const ls_table* bck, float* p_out, ls_stream_t stream);
+
+/* DistMat (Eq. distmat): d_out device float [N][N], d_ji = -(log(p_ji v eps) + log(p_ij v eps))/2,
+ * d_ii = 0, eps = DBL_EPSILON.  Needs tables over all N targets (LS_ERR_RANGE otherwise). */
+int ls_distance(ls_ctx* ctx, const ls_table* fwd, const ls_table* bck, float* d_out, ls_stream_t stream);
+
+/* Fused all-vs-all pipeline: forward over all L loci, backward over all L loci, posterior and
+ * distance at the D loci decode_loci (host int32, strictly increasing).  d_out [D][N][N] floats,
+ * device or host memory (host: the result is copied back before the call returns).  pac_out
+ * (host, may be NULL) receives the PAC log-likelihood sum_i log P(h_i | h_-i) (Sec. 1).
+ * status_out (device uint32 [N], may be NULL) receives per-target status bits.  Uses library-
+ * owned scratch of D*N*N floats (cached in the context).  Synchronous when pac_out is given or
+ * d_out is host memory; returns LS_WARN_* when such a call saw underflow/overflow. */
+int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out, double* pac_out,
+               uint32_t* status_out, ls_stream_t stream);
+
+/* ---- profiling (tracing hook) ------------------------------------------------------------ */
+
+/* Enable (1) or disable (0) phase timing of ls_run_all on this context.  When enabled, each
+ * ls_run_all records CUDA events on its stream before and after its four phases. */
+int ls_set_profiling(ls_ctx* ctx, int32_t enable);
+
+/* Device durations of the phases of the last profiled ls_run_all, in milliseconds (ms [4]) and
+ * the number of kernels each phase launched (launches [4], may be NULL): 0 forward propagation,
+ * 1 backward propagation (with the in-place alpha*beta products at the decode loci), 2 posterior
+ * normalisation into half distances, 3 symmetrisation.  Waits for the last recorded event. */
+int ls_profile_read(ls_ctx* ctx, float* ms, int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LS_H */

@@ -1,0 +1,776 @@
+// ls_api.cu -- host implementation of the libls C ABI (include/ls.h): haplotype cache, parameter
+// handling, forward/backward tables, the launch planner and the fused all-vs-all pipeline.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ls.h"
+#include "ls_aux.cuh"
+#include "ls_internal.h"
+
+void ls_register_group0(std::vector<PropKernelInfo>& out);
+void ls_register_group1(std::vector<PropKernelInfo>& out);
+void ls_register_group2(std::vector<PropKernelInfo>& out);
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(x)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (x);                                                                   \
+    if (e_ != cudaSuccess) return fail(LS_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
+std::vector<PropKernelInfo>& registry() {
+  static std::vector<PropKernelInfo> v;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    ls_register_group0(v);
+    ls_register_group1(v);
+    ls_register_group2(v);
+  });
+  return v;
+}
+
+int dev_alloc(ls_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(LS_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  if (c) c->bytes += bytes;
+  return LS_OK;
+}
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// ---- launch planning -----------------------------------------------------------------------
+struct Launch {
+  const PropKernelInfo* k;
+  int t_begin, t_count, grid, smem;
+};
+
+struct Cand {
+  const PropKernelInfo* k;
+  int smem, per_sm;
+};
+
+std::vector<Cand> candidates(ls_ctx* c) {
+  std::vector<Cand> out;
+  const int N = c->N;
+  for (const auto& k : registry()) {
+    const int S = k.w * 32 / k.tpw;
+    const int Jr = (N + S - 1) / S;
+    if (Jr < k.tpw || Jr > 4 * k.kq) continue;
+    const int smem = k.smem_bytes(N, c->row_words);
+    if (smem > 227 * 1024) continue;
+    if (cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.func, k.w * 32, smem) != cudaSuccess || nb < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    out.push_back(Cand{&k, smem, nb});
+  }
+  return out;
+}
+
+// modelled time of one launch: for every wave, (CTAs per SM in that wave) x warps x (slots per
+// lane + a fixed per-locus overhead), summed over waves
+double cost_of(const Cand& cd, int count, int nsm) {
+  const long long ctas = (count + cd.k->tpw - 1) / cd.k->tpw;
+  const long long per_wave = (long long)nsm * cd.per_sm;
+  const long long full = ctas / per_wave, rem = ctas % per_wave;
+  const double unit = cd.k->w * (cd.k->kq + 3.0);
+  double t = (double)full * cd.per_sm * unit;
+  if (rem) t += (double)((rem + nsm - 1) / nsm) * unit;
+  return t;
+}
+
+const Cand* best_for(const std::vector<Cand>& cs, int count, int nsm, double* cost) {
+  const Cand* best = nullptr;
+  double bc = 1e300;
+  for (const auto& cd : cs) {
+    const double cc = cost_of(cd, count, nsm);
+    if (cc < bc * 0.999 || (cc <= bc * 1.001 && best && cd.k->tpw > best->k->tpw)) {
+      bc = cc;
+      best = &cd;
+    }
+  }
+  *cost = bc;
+  return best;
+}
+
+int plan(ls_ctx* c, int t_begin, int t_count, std::vector<Launch>& out) {
+  out.clear();
+  auto cs = candidates(c);
+  if (cs.empty()) return fail(LS_ERR_UNSUPPORTED, "no compiled propagation variant serves N=%d", c->N);
+  // LS_PROP_VARIANT="tpw,w,kq" restricts the planner to one compiled variant (tuning sweeps)
+  if (const char* ov = getenv("LS_PROP_VARIANT")) {
+    int a = 0, b = 0, k = 0;
+    if (sscanf(ov, "%d,%d,%d", &a, &b, &k) == 3) {
+      std::vector<Cand> keep;
+      for (const auto& cd : cs)
+        if (cd.k->tpw == a && cd.k->w == b && cd.k->kq == k) keep.push_back(cd);
+      if (keep.empty()) return fail(LS_ERR_UNSUPPORTED, "LS_PROP_VARIANT=%s does not serve N=%d", ov, c->N);
+      cs = keep;
+    }
+  }
+  double c1 = 0;
+  const Cand* b1 = best_for(cs, t_count, c->num_sms, &c1);
+  // full waves of the best variant, then the remainder with the variant best for it
+  const int per_wave_t = c->num_sms * b1->per_sm * b1->k->tpw;
+  if (t_count > per_wave_t && t_count % per_wave_t != 0) {
+    const int main_t = (t_count / per_wave_t) * per_wave_t;
+    double cm = 0, ct = 0;
+    const Cand* bm = b1;
+    cm = cost_of(*bm, main_t, c->num_sms);
+    const Cand* bt = best_for(cs, t_count - main_t, c->num_sms, &ct);
+    if (cm + ct < c1) {
+      out.push_back(Launch{bm->k, t_begin, main_t, main_t / bm->k->tpw, bm->smem});
+      const int tt = t_count - main_t;
+      out.push_back(Launch{bt->k, t_begin + main_t, tt, (tt + bt->k->tpw - 1) / bt->k->tpw, bt->smem});
+      return LS_OK;
+    }
+  }
+  out.push_back(Launch{b1->k, t_begin, t_count, (t_count + b1->k->tpw - 1) / b1->k->tpw, b1->smem});
+  return LS_OK;
+}
+
+void base_params(ls_ctx* c, lsk::PropParams& p, int dir) {
+  memset(&p, 0, sizeof p);
+  p.bits = c->bits;
+  p.row_words = c->row_words;
+  p.N = c->N;
+  p.L = c->L;
+  p.dir = dir;
+  p.omr = c->omr;
+  p.rr = dir == 0 ? c->rr_f : c->rr_b;
+  p.thm = c->thm;
+  p.thx = c->thx;
+  p.pi_u = c->pi_u;
+  p.err = c->err;
+}
+
+int run_launches(ls_ctx* c, lsk::PropParams p, int t_begin, int t_count, cudaStream_t s, int* nlaunch = nullptr) {
+  std::vector<Launch> lp;
+  int rc = plan(c, t_begin, t_count, lp);
+  if (rc) return rc;
+  if (nlaunch) *nlaunch = (int)lp.size();
+  for (const auto& L : lp) {
+    p.t_begin = L.t_begin;
+    p.t_count = L.t_count;
+    cudaError_t e = L.k->launch(p, L.grid, L.smem, s);
+    if (e != cudaSuccess) return fail(LS_ERR_CUDA, "propagation launch (TPW=%d W=%d KQ=%d): %s", L.k->tpw, L.k->w, L.k->kq,
+                                      cudaGetErrorString(e));
+  }
+  return LS_OK;
+}
+
+int check_ctx(const ls_ctx* c) {
+  if (!c) return fail(LS_ERR_ARG, "null context");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(LS_ERR_CUDA, "cudaSetDevice(%d) failed", c->device);
+  return LS_OK;
+}
+
+int init_ctx_common(ls_ctx* c) {
+  CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  int rc = dev_alloc(c, (void**)&c->err, sizeof(int));
+  if (rc) return rc;
+  CUDA_TRY(cudaMemset(c->err, 0, sizeof(int)));
+  rc = dev_alloc(c, (void**)&c->logs_scratch, sizeof(double) * c->N);
+  if (rc) return rc;
+  return dev_alloc(c, (void**)&c->status_scratch, sizeof(uint32_t) * c->N);
+}
+
+void free_ctx(ls_ctx* c) {
+  if (!c) return;
+  cudaFree(c->bits);
+  cudaFree(c->omr);
+  cudaFree(c->rr_f);
+  cudaFree(c->rr_b);
+  cudaFree(c->thm);
+  cudaFree(c->thx);
+  cudaFree(c->Pi);
+  cudaFree(c->logs_scratch);
+  cudaFree(c->status_scratch);
+  cudaFree(c->err);
+  cudaFree(c->dscratch);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+int read_err_word(ls_ctx* c, cudaStream_t s) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h) {
+    cudaMemsetAsync(c->err, 0, sizeof(int), s);
+    return fail(LS_ERR_DEVICE, "a device wait for staged haplotype rows ran out of time");
+  }
+  return LS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+const char* ls_version(void) {
+  return "libls 0.1 for sm_103a: LS all-vs-all forward/backward (FP32 f32x2 tiles, TMA-staged rows), "
+         "posterior, distance";
+}
+
+const char* ls_last_error(void) { return g_err.c_str(); }
+
+int ls_create(ls_ctx** out, const uint8_t* haps, int32_t N, int32_t L) {
+  if (!out || !haps) return fail(LS_ERR_ARG, "null pointer");
+  if (N < 2 || L < 1) return fail(LS_ERR_ARG, "need N >= 2 and L >= 1 (got N=%d, L=%d)", N, L);
+  ls_ctx* c = new ls_ctx;
+  *out = nullptr;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return fail(LS_ERR_CUDA, "no CUDA device");
+  }
+  c->N = N;
+  c->L = L;
+  c->row_words = lsk::round_up((N + 31) / 32 + 1, 4);
+  int rc = dev_alloc(c, (void**)&c->bits, sizeof(uint32_t) * (size_t)L * c->row_words);
+  if (rc) { free_ctx(c); return rc; }
+  uint8_t* tmp = nullptr;
+  rc = dev_alloc(nullptr, (void**)&tmp, (size_t)N * L);
+  if (rc) { free_ctx(c); return rc; }
+  cudaError_t e = cudaMemset(c->bits, 0, sizeof(uint32_t) * (size_t)L * c->row_words);
+  if (e == cudaSuccess) e = cudaMemcpy(tmp, haps, (size_t)N * L, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const long long threads = (long long)((N + 31) / 32) * L * 32;
+    lsk::pack_kernel<<<(unsigned)((threads + 255) / 256), 256>>>(tmp, N, L, c->row_words, c->bits);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(tmp);
+  if (e != cudaSuccess) { free_ctx(c); return fail(LS_ERR_CUDA, "packing haplotypes: %s", cudaGetErrorString(e)); }
+  rc = init_ctx_common(c);
+  if (rc) { free_ctx(c); return rc; }
+  *out = c;
+  return LS_OK;
+}
+
+int ls_create_packed(ls_ctx** out, const uint32_t* packed, int32_t N, int32_t L, int32_t row_words) {
+  if (!out || !packed) return fail(LS_ERR_ARG, "null pointer");
+  if (N < 2 || L < 1 || row_words < (N + 31) / 32) return fail(LS_ERR_ARG, "bad sizes N=%d L=%d row_words=%d", N, L, row_words);
+  ls_ctx* c = new ls_ctx;
+  *out = nullptr;
+  cudaGetDevice(&c->device);
+  c->N = N;
+  c->L = L;
+  c->row_words = lsk::round_up((N + 31) / 32 + 1, 4);
+  int rc = dev_alloc(c, (void**)&c->bits, sizeof(uint32_t) * (size_t)L * c->row_words);
+  if (rc) { free_ctx(c); return rc; }
+  const int nw = (N + 31) / 32;
+  cudaError_t e = cudaMemset(c->bits, 0, sizeof(uint32_t) * (size_t)L * c->row_words);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(c->bits, sizeof(uint32_t) * c->row_words, packed, sizeof(uint32_t) * row_words, sizeof(uint32_t) * nw, L,
+                     cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess && (N & 31)) {
+    // clear the bits beyond N in the last word of every row
+    std::vector<uint32_t> col(L);
+    e = cudaMemcpy2D(col.data(), 4, c->bits + nw - 1, sizeof(uint32_t) * c->row_words, 4, L, cudaMemcpyDeviceToHost);
+    for (auto& w : col) w &= (1u << (N & 31)) - 1u;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2D(c->bits + nw - 1, sizeof(uint32_t) * c->row_words, col.data(), 4, 4, L, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) { free_ctx(c); return fail(LS_ERR_CUDA, "copying packed haplotypes: %s", cudaGetErrorString(e)); }
+  rc = init_ctx_common(c);
+  if (rc) { free_ctx(c); return rc; }
+  *out = c;
+  return LS_OK;
+}
+
+int ls_destroy(ls_ctx* ctx) {
+  if (!ctx) return fail(LS_ERR_ARG, "null context");
+  if (ctx->ntables) return fail(LS_ERR_STATE, "%d tables still alive", ctx->ntables);
+  cudaSetDevice(ctx->device);
+  free_ctx(ctx);
+  return LS_OK;
+}
+
+int ls_info(const ls_ctx* ctx, int32_t* N, int32_t* L, int32_t* row_words, size_t* device_bytes) {
+  if (!ctx) return fail(LS_ERR_ARG, "null context");
+  if (N) *N = ctx->N;
+  if (L) *L = ctx->L;
+  if (row_words) *row_words = ctx->row_words;
+  if (device_bytes) *device_bytes = ctx->bytes;
+  return LS_OK;
+}
+
+int ls_query(const ls_ctx* ctx, const int32_t* loci, int32_t nl, const int32_t* haps, int32_t nh, uint8_t* out) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (nl < 0 || nh < 0 || (nl && !loci) || (nh && !haps) || (nl && nh && !out)) return fail(LS_ERR_ARG, "bad query arguments");
+  for (int b = 0; b < nh; ++b)
+    if (haps[b] < 0 || haps[b] >= ctx->N) return fail(LS_ERR_ARG, "haplotype %d out of range", haps[b]);
+  std::vector<uint32_t> rowbuf(ctx->row_words);
+  for (int a = 0; a < nl; ++a) {
+    if (loci[a] < 0 || loci[a] >= ctx->L) return fail(LS_ERR_ARG, "locus %d out of range", loci[a]);
+    CUDA_TRY(cudaMemcpy(rowbuf.data(), ctx->bits + (size_t)loci[a] * ctx->row_words, sizeof(uint32_t) * ctx->row_words,
+                        cudaMemcpyDeviceToHost));
+    for (int b = 0; b < nh; ++b) out[(size_t)a * nh + b] = (rowbuf[haps[b] >> 5] >> (haps[b] & 31)) & 1u;
+  }
+  return LS_OK;
+}
+
+int ls_export_packed(const ls_ctx* ctx, uint32_t* out) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!out) return fail(LS_ERR_ARG, "null output");
+  CUDA_TRY(cudaMemcpy(out, ctx->bits, sizeof(uint32_t) * (size_t)ctx->L * ctx->row_words, cudaMemcpyDeviceToHost));
+  return LS_OK;
+}
+
+int ls_calc_rho(const double* m, int32_t n, double Ne, double gamma, double* rho_out) {
+  if (n < 0 || (n && (!m || !rho_out))) return fail(LS_ERR_ARG, "bad arguments");
+  if (!(Ne >= 0.0) || !std::isfinite(Ne) || !(gamma > 0.0) || !std::isfinite(gamma))
+    return fail(LS_ERR_ARG, "need Ne >= 0 and gamma > 0");
+  for (int k = 0; k < n; ++k) {
+    if (!(m[k] >= 0.0) || !std::isfinite(m[k])) return fail(LS_ERR_ARG, "genetic distance m[%d] = %g is not >= 0", k, m[k]);
+    rho_out[k] = -std::expm1(-Ne * std::pow(m[k], gamma));  // Eq. rho
+  }
+  return LS_OK;
+}
+
+int ls_set_params(ls_ctx* ctx, const double* rho, const double* mu, int32_t mu_len, const float* Pi, uint64_t* hash_out) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  const int N = ctx->N, L = ctx->L;
+  if ((L > 1 && !rho) || !mu) return fail(LS_ERR_ARG, "null rho or mu");
+  if (mu_len != 1 && mu_len != L) return fail(LS_ERR_ARG, "mu must have length 1 or L=%d (got %d)", L, mu_len);
+  for (int l = 0; l + 1 < L; ++l)
+    if (!(rho[l] >= 0.0 && rho[l] <= 1.0)) return fail(LS_ERR_ARG, "rho[%d] = %g is outside [0, 1]", l, rho[l]);
+  for (int l = 0; l < mu_len; ++l)
+    if (!(mu[l] >= 0.0 && mu[l] <= 1.0)) return fail(LS_ERR_ARG, "mu[%d] = %g is outside [0, 1]", l, mu[l]);
+  uint64_t h = 1469598103934665603ull;
+  h = fnv1a(h, &N, sizeof N);
+  h = fnv1a(h, &L, sizeof L);
+  if (L > 1) h = fnv1a(h, rho, sizeof(double) * (L - 1));
+  h = fnv1a(h, &mu_len, sizeof mu_len);
+  h = fnv1a(h, mu, sizeof(double) * mu_len);
+  std::vector<float> pih;
+  if (Pi) {
+    if (!is_device_ptr(Pi)) return fail(LS_ERR_ARG, "Pi must be device memory");
+    pih.resize((size_t)N * N);
+    CUDA_TRY(cudaMemcpy(pih.data(), Pi, sizeof(float) * pih.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < N; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < N; ++j) {
+        const float v = pih[(size_t)i * N + j];
+        if (!(v >= 0.0f) || !std::isfinite(v)) return fail(LS_ERR_ARG, "Pi[%d][%d] = %g is not a probability", i, j, v);
+        s += v;
+      }
+      if (pih[(size_t)i * N + i] != 0.0f) return fail(LS_ERR_ARG, "Pi[%d][%d] must be 0 (Sec. 2.1)", i, i);
+      if (std::fabs(s - 1.0) > 1e-5) return fail(LS_ERR_ARG, "prior row %d sums to %.9g, not 1", i, s);
+    }
+    h = fnv1a(h, pih.data(), sizeof(float) * pih.size());
+  }
+  // per-locus FP32 constants, rounded once from double
+  std::vector<float> omr(std::max(L - 1, 1)), rrf(std::max(L - 1, 1)), rrb(std::max(L - 1, 1)), thm(L), thx(L);
+  const double pi_u = 1.0 / (double)(N - 1);
+  for (int l = 0; l + 1 < L; ++l) {
+    omr[l] = (float)(1.0 - rho[l]);
+    rrf[l] = (float)(rho[l] * pi_u);
+    rrb[l] = (float)rho[l];
+  }
+  for (int l = 0; l < L; ++l) {
+    const double m = mu[mu_len == 1 ? 0 : l];
+    thm[l] = (float)(1.0 - m);  // App. A.3: (1-H)(1-2mu)+mu with H = 0
+    thx[l] = (float)m;          // and with H = 1
+  }
+  auto upload = [&](float*& dst, const std::vector<float>& v) -> int {
+    if (!dst) {
+      int r2 = dev_alloc(ctx, (void**)&dst, sizeof(float) * v.size());
+      if (r2) return r2;
+    }
+    CUDA_TRY(cudaMemcpy(dst, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice));
+    return LS_OK;
+  };
+  if ((rc = upload(ctx->omr, omr)) || (rc = upload(ctx->rr_f, rrf)) || (rc = upload(ctx->rr_b, rrb)) ||
+      (rc = upload(ctx->thm, thm)) || (rc = upload(ctx->thx, thx)))
+    return rc;
+  if (Pi) {
+    if (!ctx->Pi && (rc = dev_alloc(ctx, (void**)&ctx->Pi, sizeof(float) * (size_t)N * N))) return rc;
+    CUDA_TRY(cudaMemcpy(ctx->Pi, Pi, sizeof(float) * (size_t)N * N, cudaMemcpyDeviceToDevice));
+  } else if (ctx->Pi) {
+    cudaFree(ctx->Pi);
+    ctx->bytes -= sizeof(float) * (size_t)N * N;
+    ctx->Pi = nullptr;
+  }
+  ctx->pi_u = (float)pi_u;
+  ctx->hash = h;
+  ctx->have_params = true;
+  if (hash_out) *hash_out = h;
+  return LS_OK;
+}
+
+int ls_table_create(ls_ctx* ctx, int32_t kind, int32_t t_from, int32_t t_to, ls_table** out) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!out) return fail(LS_ERR_ARG, "null output");
+  if (kind != LS_FWD && kind != LS_BWD) return fail(LS_ERR_ARG, "kind must be LS_FWD or LS_BWD");
+  if (!(0 <= t_from && t_from < t_to && t_to <= ctx->N)) return fail(LS_ERR_ARG, "bad target range [%d, %d)", t_from, t_to);
+  if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
+  ls_table* t = new ls_table;
+  t->ctx = ctx;
+  t->kind = kind;
+  t->t_from = t_from;
+  t->t_to = t_to;
+  const size_t T = (size_t)(t_to - t_from);
+  if ((rc = dev_alloc(nullptr, (void**)&t->state, sizeof(float) * T * ctx->N)) ||
+      (rc = dev_alloc(nullptr, (void**)&t->logs, sizeof(double) * T))) {
+    cudaFree(t->state);
+    delete t;
+    return rc;
+  }
+  cudaMemset(t->state, 0, sizeof(float) * T * ctx->N);
+  cudaMemset(t->logs, 0, sizeof(double) * T);
+  ctx->ntables++;
+  *out = t;
+  return LS_OK;
+}
+
+int ls_table_destroy(ls_table* t) {
+  if (!t) return fail(LS_ERR_ARG, "null table");
+  cudaSetDevice(t->ctx->device);
+  cudaFree(t->state);
+  cudaFree(t->logs);
+  t->ctx->ntables--;
+  delete t;
+  return LS_OK;
+}
+
+int ls_table_copy(ls_table* dst, const ls_table* src, ls_stream_t stream) {
+  if (!dst || !src) return fail(LS_ERR_ARG, "null table");
+  if (dst->ctx != src->ctx || dst->kind != src->kind || dst->t_from != src->t_from || dst->t_to != src->t_to)
+    return fail(LS_ERR_RANGE, "tables differ in context, kind or target range");
+  cudaSetDevice(dst->ctx->device);
+  const size_t T = (size_t)(src->t_to - src->t_from);
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(dst->state, src->state, sizeof(float) * T * src->ctx->N, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dst->logs, src->logs, sizeof(double) * T, cudaMemcpyDeviceToDevice, s));
+  dst->locus = src->locus;
+  dst->hash = src->hash;
+  return LS_OK;
+}
+
+int ls_table_reset(ls_table* t) {
+  if (!t) return fail(LS_ERR_ARG, "null table");
+  t->locus = -1;
+  t->hash = 0;
+  return LS_OK;
+}
+
+int ls_table_info(const ls_table* t, int32_t* kind, int32_t* locus, int32_t* t_from, int32_t* t_to, uint64_t* hash) {
+  if (!t) return fail(LS_ERR_ARG, "null table");
+  if (kind) *kind = t->kind;
+  if (locus) *locus = t->locus;
+  if (t_from) *t_from = t->t_from;
+  if (t_to) *t_to = t->t_to;
+  if (hash) *hash = t->hash;
+  return LS_OK;
+}
+
+int ls_table_read(const ls_table* t, float* state, double* logscale, ls_stream_t stream) {
+  if (!t) return fail(LS_ERR_ARG, "null table");
+  cudaSetDevice(t->ctx->device);
+  const size_t T = (size_t)(t->t_to - t->t_from);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (state) CUDA_TRY(cudaMemcpyAsync(state, t->state, sizeof(float) * T * t->ctx->N, cudaMemcpyDeviceToDevice, s));
+  if (logscale) CUDA_TRY(cudaMemcpyAsync(logscale, t->logs, sizeof(double) * T, cudaMemcpyDeviceToDevice, s));
+  return LS_OK;
+}
+
+static int propagate(ls_ctx* ctx, ls_table* tb, int dir, int32_t to, const int32_t* store, int32_t n_store, float* out,
+                     uint32_t* status, ls_stream_t stream) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!tb || tb->ctx != ctx) return fail(LS_ERR_ARG, "table does not belong to this context");
+  if (tb->kind != (dir == 0 ? LS_FWD : LS_BWD)) return fail(LS_ERR_ARG, "wrong table kind for this direction");
+  if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
+  if (ctx->Pi) return fail(LS_ERR_UNSUPPORTED, "propagation with a prior matrix is not built yet (uniform prior only)");
+  const int L = ctx->L;
+  if (to < 0 || to >= L) return fail(LS_ERR_ARG, "locus %d out of range [0, %d)", to, L);
+  const bool init = tb->locus < 0;
+  if (!init && tb->hash != ctx->hash) return fail(LS_ERR_PARAM_MISMATCH, "table was propagated under another parameter set");
+  const int cur = tb->locus;
+  if (!init && (dir == 0 ? to < cur : to > cur))
+    return fail(LS_ERR_DIRECTION, "%s cannot move from locus %d to %d", dir == 0 ? "forward" : "backward", cur, to);
+  if (n_store < 0 || (n_store > 0 && (!store || !out))) return fail(LS_ERR_ARG, "bad store arguments");
+  // store loci: strictly monotone inside the range this call covers
+  const int lo = dir == 0 ? (init ? 0 : cur + 1) : to;
+  const int hi = dir == 0 ? to : (init ? L - 1 : cur - 1);
+  for (int k = 0; k < n_store; ++k) {
+    if (store[k] < lo || store[k] > hi) return fail(LS_ERR_ARG, "store locus %d outside [%d, %d]", store[k], lo, hi);
+    if (k && (dir == 0 ? store[k] <= store[k - 1] : store[k] >= store[k - 1]))
+      return fail(LS_ERR_ARG, "store loci must be strictly %s", dir == 0 ? "increasing" : "decreasing");
+  }
+  if (!init && to == cur) return LS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int T = tb->t_to - tb->t_from;
+  int pos = init ? -1 : cur;  // locus the table state is at
+  int k0 = 0;
+  bool first = true;
+  while (true) {
+    const int k1 = std::min(n_store, k0 + lsk::kMaxStore);
+    const int seg_end = (k1 < n_store) ? store[k1 - 1] : to;
+    lsk::PropParams p;
+    base_params(ctx, p, dir);
+    const bool seg_init = first && init;
+    if (dir == 0) {
+      p.l_first = seg_init ? 0 : pos + 1;
+      p.n_steps = seg_end - p.l_first + 1;
+    } else {
+      p.l_first = seg_init ? L - 1 : pos;  // a resumed backward step 0 re-applies theta at pos
+      p.n_steps = p.l_first - seg_end + 1;
+    }
+    p.init = seg_init ? 1 : 0;
+    p.tab_t0 = tb->t_from;
+    p.state = tb->state;
+    p.logs = tb->logs;
+    p.status = status;
+    p.state_rows = T;
+    p.load_state = seg_init ? 0 : 1;
+    p.save_state = 1;
+    p.n_store = k1 - k0;
+    for (int k = k0; k < k1; ++k) {
+      p.store_loci[k - k0] = store[k];
+      p.store_slot[k - k0] = k;
+    }
+    p.store = out;
+    if (p.n_steps > 0) {
+      rc = run_launches(ctx, p, tb->t_from, T, s);
+      if (rc) return rc;
+    }
+    pos = seg_end;
+    first = false;
+    k0 = k1;
+    if (k1 >= n_store) break;
+  }
+  tb->locus = to;
+  tb->hash = ctx->hash;
+  return LS_OK;
+}
+
+int ls_forward(ls_ctx* ctx, ls_table* fwd, int32_t to_locus, const int32_t* store_loci, int32_t n_store, float* alpha_out,
+               uint32_t* status_out, ls_stream_t stream) {
+  return propagate(ctx, fwd, 0, to_locus, store_loci, n_store, alpha_out, status_out, stream);
+}
+
+int ls_backward(ls_ctx* ctx, ls_table* bck, int32_t to_locus, const int32_t* store_loci, int32_t n_store, float* beta_out,
+                uint32_t* status_out, ls_stream_t stream) {
+  return propagate(ctx, bck, 1, to_locus, store_loci, n_store, beta_out, status_out, stream);
+}
+
+static int check_pair(ls_ctx* ctx, const ls_table* fwd, const ls_table* bck) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!fwd || !bck || fwd->ctx != ctx || bck->ctx != ctx) return fail(LS_ERR_ARG, "tables do not belong to this context");
+  if (fwd->kind != LS_FWD || bck->kind != LS_BWD) return fail(LS_ERR_ARG, "need a forward and a backward table");
+  if (fwd->t_from != bck->t_from || fwd->t_to != bck->t_to) return fail(LS_ERR_RANGE, "tables cover different targets");
+  if (fwd->locus < 0 || bck->locus < 0) return fail(LS_ERR_STATE, "table not initialised");
+  if (fwd->locus != bck->locus) return fail(LS_ERR_LOCUS_MISMATCH, "forward at locus %d, backward at %d", fwd->locus, bck->locus);
+  if (fwd->hash != bck->hash) return fail(LS_ERR_PARAM_MISMATCH, "tables were propagated under different parameters");
+  return LS_OK;
+}
+
+int ls_posterior(ls_ctx* ctx, const ls_table* fwd, const ls_table* bck, float* p_out, ls_stream_t stream) {
+  int rc = check_pair(ctx, fwd, bck);
+  if (rc) return rc;
+  if (!p_out) return fail(LS_ERR_ARG, "null output");
+  const int T = fwd->t_to - fwd->t_from;
+  lsk::posterior_kernel<<<T, 256, 0, (cudaStream_t)stream>>>(fwd->state, bck->state, ctx->N, fwd->t_from, 0, p_out);
+  CUDA_TRY(cudaGetLastError());
+  return LS_OK;
+}
+
+int ls_distance(ls_ctx* ctx, const ls_table* fwd, const ls_table* bck, float* d_out, ls_stream_t stream) {
+  int rc = check_pair(ctx, fwd, bck);
+  if (rc) return rc;
+  if (!d_out) return fail(LS_ERR_ARG, "null output");
+  if (fwd->t_from != 0 || fwd->t_to != ctx->N) return fail(LS_ERR_RANGE, "the distance matrix needs tables over all N targets");
+  const int N = ctx->N;
+  cudaStream_t s = (cudaStream_t)stream;
+  lsk::posterior_kernel<<<N, 256, 0, s>>>(fwd->state, bck->state, N, 0, 1, d_out);
+  CUDA_TRY(cudaGetLastError());
+  const int nt = (N + 31) / 32;
+  lsk::symmetrize_kernel<<<dim3(nt, nt, 1), dim3(32, 8), 0, s>>>(d_out, N);
+  CUDA_TRY(cudaGetLastError());
+  return LS_OK;
+}
+
+int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out, double* pac_out, uint32_t* status_out,
+               ls_stream_t stream) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
+  if (ctx->Pi) return fail(LS_ERR_UNSUPPORTED, "propagation with a prior matrix is not built yet (uniform prior only)");
+  const int N = ctx->N, L = ctx->L;
+  if (D < 0 || (D > 0 && (!decode_loci || !d_out))) return fail(LS_ERR_ARG, "bad decode arguments");
+  if (D > lsk::kMaxStore) return fail(LS_ERR_UNSUPPORTED, "at most %d decode loci per call", lsk::kMaxStore);
+  for (int k = 0; k < D; ++k) {
+    if (decode_loci[k] < 0 || decode_loci[k] >= L) return fail(LS_ERR_ARG, "decode locus %d out of range", decode_loci[k]);
+    if (k && decode_loci[k] <= decode_loci[k - 1]) return fail(LS_ERR_ARG, "decode loci must be strictly increasing");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool host_out = D > 0 && !is_device_ptr(d_out);
+  float* dd = d_out;
+  const size_t dbytes = sizeof(float) * (size_t)D * N * N;
+  if (host_out) {
+    if (ctx->dscratch_bytes < dbytes) {
+      cudaFree(ctx->dscratch);
+      ctx->bytes -= ctx->dscratch_bytes;
+      ctx->dscratch = nullptr;
+      ctx->dscratch_bytes = 0;
+      if ((rc = dev_alloc(ctx, (void**)&ctx->dscratch, dbytes))) return rc;
+      ctx->dscratch_bytes = dbytes;
+    }
+    dd = ctx->dscratch;
+  }
+  uint32_t* stat = ctx->status_scratch;
+  CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(uint32_t) * N, s));
+  const bool prof = ctx->profile;
+  if (prof) CUDA_TRY(cudaEventRecord(ctx->ev[0], s));
+  // forward over all loci: alpha at the decode loci goes straight into the output buffer
+  lsk::PropParams p;
+  base_params(ctx, p, 0);
+  p.l_first = 0;
+  p.n_steps = L;
+  p.init = 1;
+  p.tab_t0 = 0;
+  p.state_rows = N;
+  p.logs = ctx->logs_scratch;
+  p.status = stat;
+  p.n_store = D;
+  for (int k = 0; k < D; ++k) {
+    p.store_loci[k] = decode_loci[k];
+    p.store_slot[k] = k;
+  }
+  p.store = dd;
+  if ((rc = run_launches(ctx, p, 0, N, s, &ctx->launches[0]))) return rc;
+  if (prof) CUDA_TRY(cudaEventRecord(ctx->ev[1], s));
+  // backward over all loci: alpha * beta overwrites alpha at the decode loci
+  base_params(ctx, p, 1);
+  p.l_first = L - 1;
+  p.n_steps = L;
+  p.init = 1;
+  p.tab_t0 = 0;
+  p.state_rows = N;
+  p.status = stat;
+  p.n_store = D;
+  for (int k = 0; k < D; ++k) {
+    p.store_loci[k] = decode_loci[D - 1 - k];
+    p.store_slot[k] = D - 1 - k;
+  }
+  p.alpha_dec = dd;
+  if ((rc = run_launches(ctx, p, 0, N, s, &ctx->launches[1]))) return rc;
+  if (prof) CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
+  ctx->launches[2] = ctx->launches[3] = 0;
+  if (D > 0) {
+    lsk::decode_kernel<<<dim3(N, D), 256, 0, s>>>(dd, N);
+    CUDA_TRY(cudaGetLastError());
+    ctx->launches[2] = 1;
+  }
+  if (prof) CUDA_TRY(cudaEventRecord(ctx->ev[3], s));
+  if (D > 0) {
+    const int nt = (N + 31) / 32;
+    lsk::symmetrize_kernel<<<dim3(nt, nt, D), dim3(32, 8), 0, s>>>(dd, N);
+    CUDA_TRY(cudaGetLastError());
+    ctx->launches[3] = 1;
+  }
+  if (prof) {
+    CUDA_TRY(cudaEventRecord(ctx->ev[4], s));
+    ctx->profiled = true;
+  }
+  if (status_out) CUDA_TRY(cudaMemcpyAsync(status_out, stat, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
+  const bool sync = host_out || pac_out;
+  if (host_out) CUDA_TRY(cudaMemcpyAsync(d_out, dd, dbytes, cudaMemcpyDeviceToHost, s));
+  if (!sync) return LS_OK;
+  std::vector<double> lf(N);
+  std::vector<uint32_t> sh(N);
+  CUDA_TRY(cudaMemcpyAsync(lf.data(), ctx->logs_scratch, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(sh.data(), stat, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, s));
+  if ((rc = read_err_word(ctx, s))) return rc;
+  if (pac_out) {
+    double pac = 0.0;
+    for (int i = 0; i < N; ++i) pac += lf[i];  // PAC log-likelihood (Sec. 1), fixed order
+    *pac_out = pac;
+  }
+  uint32_t any = 0;
+  for (auto v : sh) any |= v;
+  // total underflow is reported first: the NaNs it leaves behind also trip the overflow check
+  if (any & 1u) return LS_WARN_UNDERFLOW;
+  if (any & 2u) return LS_WARN_OVERFLOW;
+  return LS_OK;
+}
+
+int ls_set_profiling(ls_ctx* ctx, int32_t enable) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (enable && !ctx->ev[0])
+    for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
+  ctx->profile = enable != 0;
+  ctx->profiled = false;
+  return LS_OK;
+}
+
+int ls_profile_read(ls_ctx* ctx, float* ms, int32_t* launches) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!ms) return fail(LS_ERR_ARG, "null output");
+  if (!ctx->profiled) return fail(LS_ERR_STATE, "no profiled ls_run_all yet");
+  CUDA_TRY(cudaEventSynchronize(ctx->ev[4]));
+  for (int k = 0; k < 4; ++k) {
+    CUDA_TRY(cudaEventElapsedTime(&ms[k], ctx->ev[k], ctx->ev[k + 1]));
+    if (launches) launches[k] = ctx->launches[k];
+  }
+  return LS_OK;
+}
+
+}  // extern "C"

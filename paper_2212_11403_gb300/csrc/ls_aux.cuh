@@ -1,0 +1,112 @@
+// ls_aux.cuh -- auxiliary kernels: haplotype bit packing, posterior/half-distance from tables and
+// the in-place symmetrisation of the distance matrix.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsk {
+
+// Pack uint8 [L][N] 0/1 haplotypes into variant-major rows of 32 haplotypes per word, haplotype i
+// in bit i%32 of word i/32 (Sec. 4.1.1).  One warp per output word: a coalesced 32-byte read and a
+// ballot.  Padding words must be zeroed beforehand.
+__global__ void pack_kernel(const uint8_t* __restrict__ h, int N, int L, int row_words, uint32_t* __restrict__ out) {
+  const int nw = (N + 31) / 32;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)nw * L) return;
+  const int l = (int)(wid / nw), w = (int)(wid % nw);
+  const int i = 32 * w + lane;
+  const bool bit = i < N && h[(size_t)l * N + i] != 0;
+  const uint32_t word = __ballot_sync(0xffffffffu, bit);
+  if (lane == 0) out[(size_t)l * row_words + w] = word;
+}
+
+// Eq. postprob from a forward table (alpha) and a backward table (beta) at the same locus, one
+// CTA per target row: p_j = alpha_j beta_j / sum_k alpha_k beta_k (eps for all j if the sum is 0),
+// p_ii = 0.  mode 0 writes p; mode 1 writes -log(max(p, eps))/2 (the half distance of Eq. distmat).
+__global__ void posterior_kernel(const float* __restrict__ alpha, const float* __restrict__ beta, int N, int t0,
+                                 int mode, float* __restrict__ out) {
+  constexpr float eps = 2.220446049250313e-16f;
+  const int r = blockIdx.x, i = t0 + r;
+  const float* a = alpha + (size_t)r * N;
+  const float* b = beta + (size_t)r * N;
+  float s = 0.0f;
+  for (int j = threadIdx.x; j < N; j += blockDim.x)
+    if (j != i) s += a[j] * b[j];
+  __shared__ float red[32];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float Z = red[0];
+  const float invZ = Z > 0.0f ? 1.0f / Z : 0.0f;
+  float* o = out + (size_t)r * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float p = j == i ? 0.0f : (Z > 0.0f ? a[j] * b[j] * invZ : eps);
+    if (mode == 1) p = j == i ? 0.0f : -0.5f * logf(fmaxf(p, eps));
+    o[j] = p;
+  }
+}
+
+// Normalise the products alpha * beta that the backward pass left at D decode loci ([D][N][N],
+// row i = recipient i) into half distances -log(max(p, eps))/2 with p of Eq. postprob, in place.
+// A zero normaliser gives p = eps for every donor (Sec. 2.2).  Grid (N, D), one CTA per row.
+__global__ void decode_kernel(float* __restrict__ prod, int N) {
+  constexpr float eps = 2.220446049250313e-16f;
+  const int r = blockIdx.x;
+  float* a = prod + ((size_t)blockIdx.y * N + r) * N;
+  float s = 0.0f;
+  for (int j = threadIdx.x; j < N; j += blockDim.x)
+    if (j != r) s += a[j];
+  __shared__ float red[32];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float Z = red[0];
+  const float invZ = Z > 0.0f ? 1.0f / Z : 0.0f;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const float p = Z > 0.0f ? a[j] * invZ : eps;
+    a[j] = j == r ? 0.0f : -0.5f * logf(fmaxf(p, eps));
+  }
+}
+
+// In-place symmetrisation of D stacked N x N matrices of half distances h: d = h + h^T with a zero
+// diagonal (Eq. distmat).  Block (bx, by) with bx <= by owns the tile pair (bx, by)/(by, bx): it
+// reads both 32x32 tiles into shared memory before writing either, so no element is read after
+// another block wrote it.  Reads and writes are 128-byte rows.
+__global__ void symmetrize_kernel(float* __restrict__ d, int N) {
+  const int bx = blockIdx.x, by = blockIdx.y;
+  if (bx > by) return;
+  float* m = d + (size_t)blockIdx.z * N * N;
+  __shared__ float A[32][33], B[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const int ra = bx * 32 + k, ca = by * 32 + tx;  // tile (bx, by)
+    const int rb = by * 32 + k, cb = bx * 32 + tx;  // tile (by, bx)
+    A[k][tx] = (ra < N && ca < N) ? m[(size_t)ra * N + ca] : 0.0f;
+    B[k][tx] = (rb < N && cb < N) ? m[(size_t)rb * N + cb] : 0.0f;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int ra = bx * 32 + k, ca = by * 32 + tx;
+    if (ra < N && ca < N) m[(size_t)ra * N + ca] = ra == ca ? 0.0f : A[k][tx] + B[tx][k];
+    if (bx != by) {
+      const int rb = by * 32 + k, cb = bx * 32 + tx;
+      if (rb < N && cb < N) m[(size_t)rb * N + cb] = B[k][tx] + A[tx][k];
+    }
+  }
+}
+
+}  // namespace lsk

@@ -1,0 +1,59 @@
+// ls_internal.h -- host-side structures shared by the libls translation units.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ls_prop.cuh"
+
+// One compiled variant of the propagation kernel: TPW targets per CTA, W warps, KQ quads per lane.
+struct PropKernelInfo {
+  int tpw, w, kq;
+  const void* func;
+  cudaError_t (*launch)(const lsk::PropParams& p, int grid, int smem, cudaStream_t s);
+  int (*smem_bytes)(int N, int row_words);
+};
+
+void ls_register_prop_kernels(std::vector<PropKernelInfo>& out);
+
+struct ls_ctx {
+  int device = 0;
+  int N = 0, L = 0, row_words = 0;
+  uint32_t* bits = nullptr;       // [L][row_words]
+  size_t bytes = 0;               // device bytes owned
+  // parameters
+  bool have_params = false;
+  uint64_t hash = 0;
+  float* omr = nullptr;           // [L-1] 1 - rho
+  float* rr_f = nullptr;          // [L-1] rho * pi (forward)
+  float* rr_b = nullptr;          // [L-1] rho (backward)
+  float* thm = nullptr;           // [L] 1 - mu
+  float* thx = nullptr;           // [L] mu
+  float* Pi = nullptr;            // [N][N] prior matrix copy (null: uniform)
+  float pi_u = 0.0f;
+  // scratch
+  double* logs_scratch = nullptr; // [N]
+  uint32_t* status_scratch = nullptr;  // [N]
+  int* err = nullptr;             // device error word
+  float* dscratch = nullptr;      // host-output staging for ls_run_all
+  size_t dscratch_bytes = 0;
+  int num_sms = 0;
+  int ntables = 0;
+  // profiling of ls_run_all phases
+  bool profile = false;
+  bool profiled = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int launches[4] = {0, 0, 0, 0};
+};
+
+struct ls_table {
+  ls_ctx* ctx = nullptr;
+  int kind = 0;
+  int t_from = 0, t_to = 0;
+  int locus = -1;
+  uint64_t hash = 0;
+  float* state = nullptr;   // [T][N]
+  double* logs = nullptr;   // [T]
+};

@@ -1,0 +1,509 @@
+// ls_prop.cuh -- propagation kernel of the LS all-vs-all recursions on sm_103a.
+//
+// One kernel serves both directions, because the rescaled recursions have the same shape:
+//   forward  (Eq. fwd1):  x_j <- theta_j (c x_j + r),  x = alpha,  c = (1-rho)/sum_j x_j,  r = rho pi
+//   backward (Eq. bck1, carried as t = beta*theta):
+//                         x_j <- theta_j (c x_j + r),  x = t,      c = (1-rho)/(pi sum_j x_j), r = rho
+// (the backward's beta is the pre-emission value c x + r, which is what the table keeps).
+//
+// Work decomposition.  A CTA owns TPW consecutive targets o..o+TPW-1 and all N donors.  Lane
+// (tl, sl) of warp w holds target tl and a slice of J = 4*KQ donor slots; the CTA's W*32/TPW
+// slices partition the donors.  Donor positions are rotated by o (position p <-> donor
+// (p + o) mod N) so that every target's own diagonal cell sits at position tl, i.e. slot tl of
+// slice 0.  The whole tile (TPW x N floats) stays in registers across loci (Sec. 4.2: each column
+// is carried to the target locus before moving on).
+//
+// Emission.  Per locus the lane turns its donors' bits into "match" bits (XOR with its target's
+// allele); a 16-entry shared-memory table maps 4 match bits to 4 emission probabilities
+// (theta = 1-mu on a match, mu on a mismatch, App. A.3), one 16-byte load per 4 cells, so a
+// cell costs three FP32 operations (FFMA, FMUL, FADD as packed f32x2 pairs).
+//
+// Padding and diagonal.  Slots beyond the slice and the diagonal slot are forced to "mismatch".
+// Those junk cells all start at 0 and see the same c, r and theta = mu, so they hold one common
+// value xs, which every lane replicates with the same FP32 operations; the exact junk total
+// n_junk * xs is subtracted from the reduced sum, and junk cells are never written out.
+//
+// Staging.  The packed haplotype row of each locus (N bits) is fetched by a TMA bulk copy into a
+// ring of shared-memory slots (mbarrier completion, time-bounded waits), then rotated by o into a
+// second shared buffer from which each lane funnel-shifts its 32-bit words.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsk {
+
+constexpr int kRing = 4;         // raw-row TMA ring depth
+constexpr int kMaxStore = 64;    // store loci per launch
+constexpr float kEps = 2.220446049250313e-16f;  // DBL_EPSILON = 2^-52, exact in FP32 (Eq. distmat)
+
+struct PropParams {
+  const uint32_t* bits;   // packed haplotypes [L][row_words]
+  int row_words;
+  int N, L;
+  int dir;                // 0 forward, 1 backward
+  int t_begin, t_count;   // targets handled by this launch (absolute ids)
+  int tab_t0;             // table row r <-> target tab_t0 + r
+  int l_first;            // locus of step 0
+  int n_steps;            // steps (loci) processed
+  int init;               // 1: step 0 is the initial locus (fwd 0 / bwd L-1), no prior state
+  const float* omr;       // [L-1] 1 - rho
+  const float* rr;        // [L-1] forward: rho * pi;  backward: rho
+  const float* thm;       // [L] 1 - mu (match)
+  const float* thx;       // [L] mu (mismatch)
+  float pi_u;             // uniform prior 1/(N-1)
+  float* state;           // [state_rows][N] table state (alpha or beta)
+  double* logs;           // [state_rows] log F / log G (may be null)
+  uint32_t* status;       // [state_rows] status bits (may be null)
+  int state_rows;
+  int load_state;         // 1: start from the table state
+  int save_state;         // 1: write the final state back
+  int n_store;
+  int store_loci[kMaxStore];  // in processing order
+  int store_slot[kMaxStore];  // output slot of each store locus
+  float* store;           // [slots][state_rows][N] alpha (fwd) / beta (bwd) at store loci
+  float* alpha_dec;       // backward decode: alpha at the same loci, same layout (may be null);
+                          // overwritten in place by alpha * beta (normalised by decode_kernel)
+  int* err;               // device error word (timeouts), may be null
+};
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk2(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(u64 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ float hsum2(u64 v) {
+  float a, b;
+  up2(v, a, b);
+  return a + b;
+}
+// Keeps the compiler from hoisting the memory operations of one quad above the previous quad's
+// (the store passes run only at store loci; without this their unrolled loads stay live at once).
+__device__ __forceinline__ void quad_fence() { asm volatile("" ::: "memory"); }
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void lds128(uint32_t addr, u64& a, u64& b) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+__device__ __forceinline__ uint32_t funnel(uint32_t lo, uint32_t hi, uint32_t s) {
+  return __funnelshift_r(lo, hi, s);  // (hi:lo) >> s, s in [0, 31]
+}
+
+// ---- mbarrier / TMA bulk copy ----------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of a ring slot, for at most ~2 s.  On timeout the CTA-wide flag is set
+// and every later wait returns at once; the kernel then runs to completion on stale data and the
+// host reports LS_ERR_DEVICE.  No thread leaves early, so CTA barriers stay consistent.
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* flag) {
+  if (*flag) return;
+  if (mbar_test(bar, parity)) return;
+  const uint64_t t0 = gtimer_ns();
+  while (!mbar_test(bar, parity)) {
+    if (*flag) return;
+    if (gtimer_ns() - t0 > 2000000000ull) {
+      *flag = 1;
+      return;
+    }
+    __nanosleep(64);
+  }
+}
+__device__ __forceinline__ void tma_row(uint32_t* dst, const uint32_t* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_tx(bar, bytes);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 32 bits of the cyclic bit string b -> h[(g + b) mod N] for a packed row (N >= 32, 0 <= g < N).
+__device__ __forceinline__ uint32_t cyclic32(const uint32_t* raw, int N, int g) {
+  const int w = g >> 5, s = g & 31;
+  uint32_t v = funnel(raw[w], raw[w + 1], (uint32_t)s);
+  const int n1 = N - g;
+  if (n1 < 32) v = (v & ((1u << n1) - 1u)) | (raw[0] << n1);
+  return v;
+}
+// Same for any N >= 1 (bit by bit); used when N < 32.
+__device__ __forceinline__ uint32_t cyclic32_slow(const uint32_t* raw, int N, int g) {
+  uint32_t v = 0;
+  for (int b = 0; b < 32; ++b) {
+    int d = (g + b) % N;
+    v |= ((raw[d >> 5] >> (d & 31)) & 1u) << b;
+  }
+  return v;
+}
+
+
+struct SmemLayout {
+  int nrot;      // words per rotated row
+  int raw_off;   // byte offsets of the regions
+  int rot_off;
+  int stg_off;
+  int total;
+};
+
+__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+template <int TPW, int W, int KQ>
+struct PropCfg {
+  static constexpr int SPW = 32 / TPW;     // slices per warp
+  static constexpr int S = W * SPW;        // slices per CTA
+  static constexpr int J = 4 * KQ;         // slots per lane
+  static constexpr int NWORD = (J + 31) / 32;
+  static constexpr int NCHUNK = (KQ + 7) / 8;  // 8-quad chunks staged through shared memory
+  static constexpr int THREADS = W * 32;
+  static constexpr int MINB = 2;           // two co-resident CTAs per SM hide each other's barriers
+  static constexpr int STG_STRIDE = 36;    // floats per thread in the staging chunk (16-B aligned, conflict-free)
+  // shared memory: [0,1024) emission tables (at a 512-aligned address inside), mbarriers,
+  // partial sums, timeout flag, raw-row ring, rotated rows, store/load staging
+  static constexpr int BAR_OFF = 1024;
+  static constexpr int PART_OFF = BAR_OFF + kRing * 8;
+  static constexpr int LOG_OFF = PART_OFF + 2 * TPW * W * 4;   // per-target log scale (double)
+  static constexpr int ST_OFF = LOG_OFF + TPW * 8;              // per-target status bits
+  static constexpr int FLAG_OFF = ST_OFF + TPW * 4;
+  static constexpr int RAW_OFF = ((FLAG_OFF + 16 + 127) / 128) * 128;
+  __host__ __device__ static SmemLayout layout(int N, int row_words) {
+    SmemLayout s;
+    s.nrot = (N + J + 31) / 32 + 2;
+    s.raw_off = RAW_OFF;
+    s.rot_off = RAW_OFF + round_up(kRing * row_words * 4, 128);
+    s.stg_off = s.rot_off + round_up(2 * s.nrot * 4, 128);
+    s.total = s.stg_off + THREADS * STG_STRIDE * 4;
+    return s;
+  }
+};
+
+// Slice geometry: S slices over N rotated positions; slice sigma has len positions starting at
+// start; the last mshort slices are one shorter.
+__device__ __forceinline__ void slice_of(int sigma, int S, int N, int& start, int& len) {
+  const int Jr = (N + S - 1) / S;
+  const int mshort = S * Jr - N;
+  len = Jr - (sigma >= S - mshort ? 1 : 0);
+  start = sigma * Jr - (sigma > S - mshort ? sigma - (S - mshort) : 0);
+}
+
+template <int TPW, int W, int KQ>
+__global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) {
+  using C = PropCfg<TPW, W, KQ>;
+  constexpr int SPW = C::SPW, S = C::S, NWORD = C::NWORD, THREADS = C::THREADS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int N = p.N;
+  const SmemLayout lay = C::layout(N, p.row_words);
+  float* part = reinterpret_cast<float*>(smem + C::PART_OFF);
+  volatile int* flag = reinterpret_cast<volatile int*>(smem + C::FLAG_OFF);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
+  const uint32_t smem_base = smem_u32(smem);
+  float* lutf = reinterpret_cast<float*>(smem + (((smem_base + 511u) & ~511u) - smem_base));
+  uint32_t* raw = reinterpret_cast<uint32_t*>(smem + lay.raw_off);
+  uint32_t* rot = reinterpret_cast<uint32_t*>(smem + lay.rot_off);
+  float* stg = reinterpret_cast<float*>(smem + lay.stg_off);
+  const int nrot = lay.nrot;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int tl = lane % TPW;
+  const int sl = lane / TPW;
+  const int o = p.t_begin + blockIdx.x * TPW;  // first target of this CTA (< N)
+  int start, len;
+  slice_of(warp * SPW + sl, S, N, start, len);
+  const int wbase = start >> 5;
+  const uint32_t wshift = (uint32_t)(start & 31);
+  const float n_junk = (float)(S * C::J - (N - 1));
+  // the diagonal of target tl is rotated position tl = slot tl of slice 0 (host: slice 0 >= TPW)
+  const uint32_t dclear = (warp == 0 && sl == 0) ? ~(1u << tl) : 0xffffffffu;
+  const int step_dir = p.dir == 0 ? 1 : -1;
+  const uint32_t row_bytes = (uint32_t)p.row_words * 4u;
+
+  // ---- staged transfers between the register tile and global memory (store loci only) ------
+  // element (src thread, slot s of chunk c) <-> donor (start_src + 32c + s + o) mod N of target
+  // o + tl_src; consecutive threads take consecutive slots, so global accesses are contiguous.
+  auto xfer = [&](int c, float* gbase, int mode, bool to_global) {
+    for (int idx = tid; idx < THREADS * 32; idx += THREADS) {
+      const int src = idx >> 5, s = idx & 31;
+      const int ln = src & 31;
+      const int t_s = ln % TPW, sg = (src >> 5) * SPW + ln / TPW;
+      int st, ln_s;
+      slice_of(sg, S, N, st, ln_s);
+      const int gs = 32 * c + s;
+      const int tgt = o + t_s;
+      float* sp = stg + src * C::STG_STRIDE + s;
+      const bool diag = sg == 0 && gs == t_s;
+      const bool ok = gs < ln_s && tgt < p.t_begin + p.t_count;
+      int d = st + gs + o;
+      d = d >= N ? d - N : d;
+      d = d >= N ? d - N : d;
+      float* g = gbase + (size_t)(tgt - p.tab_t0) * N;
+      if (to_global) {
+        if (ok) {
+          const float v = diag ? 0.0f : *sp;
+          if (mode == 2) g[d] = diag ? 0.0f : g[d] * v;
+          else g[d] = v;
+        }
+      } else {
+        *sp = (ok && !diag) ? g[d] : 0.0f;
+      }
+    }
+  };
+
+  // ---- prologue: barriers, first TMA copies, rotated row and emission table of step 0 --------
+  if (tid == 0) {
+    *flag = 0;
+    for (int s = 0; s < kRing; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < kRing && s < p.n_steps; ++s) {
+      const int l = p.l_first + step_dir * s;
+      tma_row(raw + s * p.row_words, p.bits + (size_t)l * p.row_words, row_bytes, &bars[s]);
+    }
+  }
+  auto build = [&](int step, int par) {
+    const int l = p.l_first + step_dir * step;
+    mbar_wait_bounded(&bars[step % kRing], (uint32_t)((step / kRing) & 1), flag);
+    const uint32_t* src = raw + (step % kRing) * p.row_words;
+    uint32_t* dst = rot + par * nrot;
+    for (int q = tid; q < nrot; q += THREADS) {
+      int g = 32 * q + o;
+      while (g >= N) g -= N;
+      dst[q] = N >= 32 ? cyclic32(src, N, g) : cyclic32_slow(src, N, g);
+    }
+    if (tid < 64) {
+      const int e = tid >> 2, k = tid & 3;
+      lutf[par * 64 + tid] = ((e >> k) & 1) ? p.thm[l] : p.thx[l];
+    }
+  };
+  build(0, 0);
+  __syncthreads();
+
+  // ---- the register tile ------------------------------------------------------------------
+  u64 x[KQ][2];
+#pragma unroll
+  for (int k = 0; k < KQ; ++k) x[k][0] = x[k][1] = 0ull;
+  if (p.load_state) {
+#pragma unroll
+    for (int c = 0; c < C::NCHUNK; ++c) {
+      xfer(c, p.state, 0, false);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = 8 * c + q;
+        if (k < KQ) {
+          const float* sp = stg + tid * C::STG_STRIDE + 4 * q;
+          x[k][0] = pk2(sp[0], sp[1]);
+          x[k][1] = pk2(sp[2], sp[3]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // store the tile (mode 0: x; 1: c x + r; 2: multiply the destination by c x + r)
+  auto store_tile = [&](float* gbase, int mode, float c, float r) {
+    const u64 C2 = pk2(c, c), R2 = pk2(r, r);
+#pragma unroll
+    for (int cc = 0; cc < C::NCHUNK; ++cc) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = 8 * cc + q;
+        if (k < KQ) {
+          const u64 a = mode == 0 ? x[k][0] : ffma2(C2, x[k][0], R2);
+          const u64 b = mode == 0 ? x[k][1] : ffma2(C2, x[k][1], R2);
+          float* sp = stg + tid * C::STG_STRIDE + 4 * q;
+          float v0, v1, v2, v3;
+          up2(a, v0, v1);
+          up2(b, v2, v3);
+          *reinterpret_cast<float4*>(sp) = make_float4(v0, v1, v2, v3);
+        }
+      }
+      __syncthreads();
+      xfer(cc, gbase, mode, true);
+      __syncthreads();
+    }
+  };
+
+  // per-target log scale and status live in shared memory, touched by threads tid < TPW only
+  double* lgs = reinterpret_cast<double*>(smem + C::LOG_OFF);
+  uint32_t* sts = reinterpret_cast<uint32_t*>(smem + C::ST_OFF);
+  if (tid < TPW) {
+    lgs[tid] = (o + tid < p.t_begin + p.t_count && p.logs && !p.init) ? p.logs[o + tid - p.tab_t0] : 0.0;
+    sts[tid] = 0u;
+  }
+  float sig_prev = 1.0f;  // previous normaliser (fwd: sum alpha; bwd: S)
+  float xs = 0.0f;        // common value of the junk cells
+
+  // reduce one value per lane over the layout; returns the CTA total for target tl
+  auto reduce = [&](float v, float* buf) -> float {
+#pragma unroll
+    for (int off = TPW; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (sl == 0) buf[tl * W + warp] = v;
+    __syncthreads();
+    float t = 0.0f;
+#pragma unroll
+    for (int w = 0; w < W; ++w) t += buf[tl * W + w];
+    return t;
+  };
+
+  if (p.load_state && p.dir == 0) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) s += hsum2(x[k][0]) + hsum2(x[k][1]);
+    sig_prev = reduce(s, part + TPW * W);
+    __syncthreads();
+  }
+
+  // per-step scalars, loaded one step ahead
+  float nx_omr = 0.f, nx_rr = 0.f, nx_thx = p.thx[p.l_first];
+  {
+    const int li = p.dir == 0 ? p.l_first - 1 : p.l_first;
+    if (li >= 0 && li < p.L - 1) {
+      nx_omr = p.omr[li];
+      nx_rr = p.rr[li];
+    }
+  }
+  int store_next = 0;
+  for (int step = 0; step < p.n_steps; ++step) {
+    const int par = step & 1;
+    const int l = p.l_first + step_dir * step;
+    const float cur_omr = nx_omr, cur_rr = nx_rr, cur_thx = nx_thx;
+    if (step + 1 < p.n_steps) {
+      const int ln = l + step_dir;
+      const int li = p.dir == 0 ? ln - 1 : ln;
+      nx_omr = p.omr[li];
+      nx_rr = p.rr[li];
+      nx_thx = p.thx[ln];
+    }
+    // refill the ring slot freed by the previous step
+    if (tid == 0 && step + kRing < p.n_steps) {
+      const int s2 = step + kRing;
+      const int l2 = p.l_first + step_dir * s2;
+      tma_row(raw + (s2 % kRing) * p.row_words, p.bits + (size_t)l2 * p.row_words, row_bytes, &bars[s2 % kRing]);
+    }
+    float c, r;
+    bool add_log_prev = false;
+    if (step == 0 && p.init) {
+      c = 0.0f;
+      r = p.dir == 0 ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
+    } else if (step == 0 && p.dir == 1) {
+      c = 1.0f;  // backward resume: x = theta^l beta^l from the stored beta
+      r = 0.0f;
+    } else {
+      c = __fdiv_rn(cur_omr, sig_prev);  // interval l-1 (fwd) or l (bwd)
+      r = cur_rr;
+      add_log_prev = p.dir == 1;
+    }
+    const bool is_store = store_next < p.n_store && p.store_loci[store_next] == l;
+    const bool save_here = p.save_state && step == p.n_steps - 1;
+
+    if (p.dir == 1 && (is_store || save_here)) {
+      // beta^l = c t^{l+1} + rho, the pre-emission value; when decoding, alpha^l beta^l
+      // overwrites alpha^l in place (normalised by the decode kernel)
+      const int slot = is_store ? p.store_slot[store_next] : 0;
+      if (is_store && p.store) store_tile(p.store + (size_t)slot * p.state_rows * N, 1, c, r);
+      if (is_store && p.alpha_dec) store_tile(p.alpha_dec + (size_t)slot * p.state_rows * N, 2, c, r);
+      if (save_here) store_tile(p.state, 1, c, r);
+    }
+
+    // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
+    const uint32_t* rw = rot + par * nrot;
+    const uint32_t inv = ((rw[0] >> tl) & 1u) ? 0u : 0xffffffffu;  // target allele at l (position tl)
+    uint32_t wm[NWORD];
+#pragma unroll
+    for (int m = 0; m < NWORD; ++m) {
+      const int v = len - 32 * m;
+      const uint32_t vm = v >= 32 ? 0xffffffffu : (v <= 0 ? 0u : ((1u << v) - 1u));
+      uint32_t w = (funnel(rw[wbase + m], rw[wbase + m + 1], wshift) ^ inv) & vm;
+      if (m == 0) w &= dclear;
+      wm[m] = w;
+    }
+    const uint32_t lut_base = smem_u32(lutf + par * 64);
+    const u64 C2 = pk2(c, c), R2 = pk2(r, r);
+    u64 acc0 = 0ull, acc1 = 0ull;
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+      const uint32_t w = wm[k >> 3];
+      const int q = k & 7;
+      const uint32_t off = q == 0 ? (w << 4) : (w >> (4 * q - 4));
+      u64 th01, th23;
+      lds128((off & 0xf0u) | lut_base, th01, th23);
+      const u64 u01 = ffma2(C2, x[k][0], R2);
+      const u64 u23 = ffma2(C2, x[k][1], R2);
+      x[k][0] = fmul2(th01, u01);
+      x[k][1] = fmul2(th23, u23);
+      acc0 = fadd2(acc0, x[k][0]);
+      acc1 = fadd2(acc1, x[k][1]);
+    }
+    xs = cur_thx * fmaf(c, xs, r);  // junk cells: theta = mu in every lane
+
+    if (p.dir == 0 && (is_store || save_here)) {
+      if (is_store && p.store) store_tile(p.store + (size_t)p.store_slot[store_next] * p.state_rows * N, 0, 0.f, 0.f);
+      if (save_here) store_tile(p.state, 0, 0.f, 0.f);
+    }
+    if (is_store) ++store_next;
+
+    if (step + 1 < p.n_steps) build(step + 1, par ^ 1);  // stage the next locus
+
+    const float tot = reduce(hsum2(acc0) + hsum2(acc1), part + par * TPW * W);
+    float sig = tot - n_junk * xs;
+    if (p.dir == 1) sig *= p.pi_u;
+    if (tid < TPW) {
+      uint32_t stb = 0u;
+      if (sig < 1.17549435e-38f) stb |= 1u;        // LS_STATUS_UNDERFLOW: zero or subnormal normaliser
+      if (!(sig <= 3.40282347e+38f)) stb |= 2u;    // LS_STATUS_OVERFLOW: infinite or NaN normaliser
+      if (stb) sts[tid] |= stb;
+      if (p.dir == 0) lgs[tid] += (double)logf(sig);
+      else if (add_log_prev) lgs[tid] += (double)logf(sig_prev);
+    }
+    sig_prev = sig;
+  }
+
+  if (tid < TPW && o + tid < p.t_begin + p.t_count) {
+    const int row = o + tid - p.tab_t0;
+    const uint32_t stb = sts[tid] | (*flag ? 4u : 0u);  // 4 = LS_STATUS_TIMEOUT
+    if (p.logs) p.logs[row] = lgs[tid];
+    if (p.status && stb) atomicOr(p.status + row, stb);
+    if (*flag && p.err) atomicOr(p.err, 1);
+  }
+}
+
+}  // namespace lsk
