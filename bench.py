@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample size, in seconds of CPU work")
     ap.add_argument("--N", type=int, default=None, help="override N (small cases for profiling; not a bench line)")
     ap.add_argument("--L", type=int, default=None, help="override L (small cases for profiling; not a bench line)")
+    ap.add_argument("--D", type=int, default=None, help="override the number of decode loci (profiling cases)")
     return ap.parse_args()
 
 
@@ -203,6 +204,9 @@ def main():
     from paper_2212_11403_gb300 import ls
 
     w = make_inputs(args.workload, args.N, args.L)
+    if args.D:
+        from paper_2212_11403_gb300 import synth
+        w["loci"] = synth.decode_loci(w["L"], args.D)
     N, L, loci = w["N"], w["L"], w["loci"]
     D = len(loci)
     cells = float(N) * N * L

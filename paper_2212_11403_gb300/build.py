@@ -25,10 +25,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
 # (source, extra defines, object name)
 UNITS = [
     ("ls_api.cu", [], "ls_api.o"),
-    ("ls_prop_inst.cu", ["-DLS_INST_GROUP=0"], "ls_prop_g0.o"),
-    ("ls_prop_inst.cu", ["-DLS_INST_GROUP=1"], "ls_prop_g1.o"),
-    ("ls_prop_inst.cu", ["-DLS_INST_GROUP=2"], "ls_prop_g2.o"),
-]
+] + [("ls_prop_inst.cu", ["-DLS_INST_GROUP=%d" % g], "ls_prop_g%d.o" % g) for g in range(6)]
 
 
 def nvcc() -> str:

@@ -17,6 +17,9 @@
 void ls_register_group0(std::vector<PropKernelInfo>& out);
 void ls_register_group1(std::vector<PropKernelInfo>& out);
 void ls_register_group2(std::vector<PropKernelInfo>& out);
+void ls_register_group3(std::vector<PropKernelInfo>& out);
+void ls_register_group4(std::vector<PropKernelInfo>& out);
+void ls_register_group5(std::vector<PropKernelInfo>& out);
 
 namespace {
 
@@ -45,6 +48,9 @@ std::vector<PropKernelInfo>& registry() {
     ls_register_group0(v);
     ls_register_group1(v);
     ls_register_group2(v);
+    ls_register_group3(v);
+    ls_register_group4(v);
+    ls_register_group5(v);
   });
   return v;
 }
@@ -85,17 +91,15 @@ std::vector<Cand> candidates(ls_ctx* c) {
   std::vector<Cand> out;
   const int N = c->N;
   for (const auto& k : registry()) {
-    const int S = k.w * 32 / k.tpw;
-    const int Jr = (N + S - 1) / S;
-    if (Jr < k.tpw || Jr > 4 * k.kq) continue;
-    const int smem = k.smem_bytes(N, c->row_words);
+    if (!k.serves(N)) continue;
+    const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;
-    if (cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
+    bool ok = true;
+    for (int d = 0; d < 2 && ok; ++d)
+      if (cudaFuncSetAttribute(k.func[d], cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) ok = false;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.func, k.w * 32, smem) != cudaSuccess || nb < 1) {
+    if (ok && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.func[0], k.w * 32, smem) != cudaSuccess || nb < 1)) ok = false;
+    if (!ok) {
       cudaGetLastError();
       continue;
     }
@@ -168,11 +172,12 @@ int plan(ls_ctx* c, int t_begin, int t_count, std::vector<Launch>& out) {
 
 void base_params(ls_ctx* c, lsk::PropParams& p, int dir) {
   memset(&p, 0, sizeof p);
-  p.bits = c->bits;
-  p.row_words = c->row_words;
+  p.bits2 = c->bits2;
+  p.rw2 = c->rw2;
   p.N = c->N;
   p.L = c->L;
   p.dir = dir;
+  p.mu_vec = c->mu_vec;
   p.omr = c->omr;
   p.rr = dir == 0 ? c->rr_f : c->rr_b;
   p.thm = c->thm;
@@ -189,7 +194,7 @@ int run_launches(ls_ctx* c, lsk::PropParams p, int t_begin, int t_count, cudaStr
   for (const auto& L : lp) {
     p.t_begin = L.t_begin;
     p.t_count = L.t_count;
-    cudaError_t e = L.k->launch(p, L.grid, L.smem, s);
+    cudaError_t e = L.k->launch(p.dir, p, L.grid, L.smem, s);
     if (e != cudaSuccess) return fail(LS_ERR_CUDA, "propagation launch (TPW=%d W=%d KQ=%d): %s", L.k->tpw, L.k->w, L.k->kq,
                                       cudaGetErrorString(e));
   }
@@ -204,7 +209,17 @@ int check_ctx(const ls_ctx* c) {
 
 int init_ctx_common(ls_ctx* c) {
   CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-  int rc = dev_alloc(c, (void**)&c->err, sizeof(int));
+  // doubled rows: 2N bits per locus plus room for a lane's funnel-shift overrun
+  c->rw2 = lsk::round_up((2 * c->N + 31) / 32 + 6, 4);
+  int rc = dev_alloc(c, (void**)&c->bits2, sizeof(uint32_t) * (size_t)c->L * c->rw2);
+  if (rc) return rc;
+  {
+    const long long n = (long long)c->L * c->rw2;
+    lsk::double_rows_kernel<<<(unsigned)((n + 255) / 256), 256>>>(c->bits, c->row_words, c->N, c->L, c->bits2, c->rw2);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaDeviceSynchronize());
+  }
+  rc = dev_alloc(c, (void**)&c->err, sizeof(int));
   if (rc) return rc;
   CUDA_TRY(cudaMemset(c->err, 0, sizeof(int)));
   rc = dev_alloc(c, (void**)&c->logs_scratch, sizeof(double) * c->N);
@@ -215,6 +230,7 @@ int init_ctx_common(ls_ctx* c) {
 void free_ctx(ls_ctx* c) {
   if (!c) return;
   cudaFree(c->bits);
+  cudaFree(c->bits2);
   cudaFree(c->omr);
   cudaFree(c->rr_f);
   cudaFree(c->rr_b);
@@ -444,6 +460,7 @@ int ls_set_params(ls_ctx* ctx, const double* rho, const double* mu, int32_t mu_l
     ctx->Pi = nullptr;
   }
   ctx->pi_u = (float)pi_u;
+  ctx->mu_vec = mu_len > 1 ? 1 : 0;
   ctx->hash = h;
   ctx->have_params = true;
   if (hash_out) *hash_out = h;

@@ -5,7 +5,29 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ls_prop.cuh"
+
 namespace lsk {
+
+// Doubled rows for the propagation kernel: out[l][q] holds bits [32q, 32q+32) of the cyclic string
+// b -> h[l][b mod N] for b < 2N (zero beyond), so every rotated slice is one contiguous run.
+__global__ void double_rows_kernel(const uint32_t* __restrict__ bits, int rw, int N, int L, uint32_t* __restrict__ out,
+                                   int rw2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)L * rw2) return;
+  const int l = (int)(i / rw2), q = (int)(i % rw2);
+  const uint32_t* row = bits + (size_t)l * rw;
+  const long long p0 = 32ll * q;
+  uint32_t v = 0;
+  if (p0 < 2ll * N) {
+    const int g = (int)(p0 < N ? p0 : p0 - N);
+    v = N >= 32 ? cyclic32(row, N, g) : cyclic32_slow(row, N, g);
+    const long long rem = 2ll * N - p0;
+    if (rem < 32) v &= (1u << rem) - 1u;
+  }
+  out[i] = v;
+}
+
 
 // Pack uint8 [L][N] 0/1 haplotypes into variant-major rows of 32 haplotypes per word, haplotype i
 // in bit i%32 of word i/32 (Sec. 4.1.1).  One warp per output word: a coalesced 32-byte read and a

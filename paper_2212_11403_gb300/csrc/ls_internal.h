@@ -8,12 +8,14 @@
 
 #include "ls_prop.cuh"
 
-// One compiled variant of the propagation kernel: TPW targets per CTA, W warps, KQ quads per lane.
+// One compiled variant of the propagation kernel: TPW targets per CTA, W warps, KQ quads per lane
+// (forward and backward instantiations).
 struct PropKernelInfo {
   int tpw, w, kq;
-  const void* func;
-  cudaError_t (*launch)(const lsk::PropParams& p, int grid, int smem, cudaStream_t s);
-  int (*smem_bytes)(int N, int row_words);
+  const void* func[2];
+  cudaError_t (*launch)(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s);
+  int (*smem_bytes)(int rw2);
+  bool (*serves)(int N);
 };
 
 void ls_register_prop_kernels(std::vector<PropKernelInfo>& out);
@@ -21,7 +23,9 @@ void ls_register_prop_kernels(std::vector<PropKernelInfo>& out);
 struct ls_ctx {
   int device = 0;
   int N = 0, L = 0, row_words = 0;
-  uint32_t* bits = nullptr;       // [L][row_words]
+  uint32_t* bits = nullptr;       // [L][row_words], the packed cache
+  uint32_t* bits2 = nullptr;      // [L][rw2], every row doubled (2N bits) for the propagation kernel
+  int rw2 = 0;
   size_t bytes = 0;               // device bytes owned
   // parameters
   bool have_params = false;
@@ -33,6 +37,7 @@ struct ls_ctx {
   float* thx = nullptr;           // [L] mu
   float* Pi = nullptr;            // [N][N] prior matrix copy (null: uniform)
   float pi_u = 0.0f;
+  int mu_vec = 0;                 // mu given per locus
   // scratch
   double* logs_scratch = nullptr; // [N]
   uint32_t* status_scratch = nullptr;  // [N]

@@ -23,9 +23,10 @@
 // value xs, which every lane replicates with the same FP32 operations; the exact junk total
 // n_junk * xs is subtracted from the reduced sum, and junk cells are never written out.
 //
-// Staging.  The packed haplotype row of each locus (N bits) is fetched by a TMA bulk copy into a
-// ring of shared-memory slots (mbarrier completion, time-bounded waits), then rotated by o into a
-// second shared buffer from which each lane funnel-shifts its 32-bit words.
+// Staging.  Each locus row is kept in HBM twice back to back (2N bits: bit b = h[b mod N]), so the
+// bits of any slice under any rotation are one contiguous run.  TMA bulk copies move blocks of 4
+// consecutive rows into a 3-slot shared-memory ring (mbarrier completion, time-bounded waits);
+// each lane funnel-shifts its 32-bit words straight out of the staged rows.
 #pragma once
 
 #include <cstdint>
@@ -33,15 +34,16 @@
 
 namespace lsk {
 
-constexpr int kRing = 4;         // raw-row TMA ring depth
+constexpr int kSlots = 3;        // TMA ring slots
+constexpr int kRB = 4;           // consecutive rows per TMA block
 constexpr int kMaxStore = 64;    // store loci per launch
 constexpr float kEps = 2.220446049250313e-16f;  // DBL_EPSILON = 2^-52, exact in FP32 (Eq. distmat)
 
 struct PropParams {
-  const uint32_t* bits;   // packed haplotypes [L][row_words]
-  int row_words;
+  const uint32_t* bits2;  // doubled packed rows [L][rw2]: bit b of row l = h[l][b mod N], b < 2N
+  int rw2;
   int N, L;
-  int dir;                // 0 forward, 1 backward
+  int dir;                // 0 forward, 1 backward (selects the instantiation on the host)
   int t_begin, t_count;   // targets handled by this launch (absolute ids)
   int tab_t0;             // table row r <-> target tab_t0 + r
   int l_first;            // locus of step 0
@@ -51,6 +53,7 @@ struct PropParams {
   const float* rr;        // [L-1] forward: rho * pi;  backward: rho
   const float* thm;       // [L] 1 - mu (match)
   const float* thx;       // [L] mu (mismatch)
+  int mu_vec;             // 1: mu differs between loci (the emission table is rebuilt every locus)
   float pi_u;             // uniform prior 1/(N-1)
   float* state;           // [state_rows][N] table state (alpha or beta)
   double* logs;           // [state_rows] log F / log G (may be null)
@@ -103,8 +106,9 @@ __device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// 16-byte shared load as two f32x2 pairs (not volatile: the compiler may hoist it ahead of use)
 __device__ __forceinline__ void lds128(uint32_t addr, u64& a, u64& b) {
-  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+  asm("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }
 __device__ __forceinline__ uint32_t funnel(uint32_t lo, uint32_t hi, uint32_t s) {
   return __funnelshift_r(lo, hi, s);  // (hi:lo) >> s, s in [0, 31]
@@ -156,7 +160,7 @@ __device__ __forceinline__ void tma_row(uint32_t* dst, const uint32_t* src, uint
       : "memory");
 }
 
-// 32 bits of the cyclic bit string b -> h[(g + b) mod N] for a packed row (N >= 32, 0 <= g < N).
+// 32 bits of the cyclic bit string b -> h[(g + b) mod N] of a packed row (N >= 32, 0 <= g < N).
 __device__ __forceinline__ uint32_t cyclic32(const uint32_t* raw, int N, int g) {
   const int w = g >> 5, s = g & 31;
   uint32_t v = funnel(raw[w], raw[w + 1], (uint32_t)s);
@@ -175,10 +179,9 @@ __device__ __forceinline__ uint32_t cyclic32_slow(const uint32_t* raw, int N, in
 }
 
 
+
 struct SmemLayout {
-  int nrot;      // words per rotated row
-  int raw_off;   // byte offsets of the regions
-  int rot_off;
+  int ring_off;  // byte offsets of the regions
   int stg_off;
   int total;
 };
@@ -193,52 +196,60 @@ struct PropCfg {
   static constexpr int NWORD = (J + 31) / 32;
   static constexpr int NCHUNK = (KQ + 7) / 8;  // 8-quad chunks staged through shared memory
   static constexpr int THREADS = W * 32;
-  static constexpr int MINB = 2;           // two co-resident CTAs per SM hide each other's barriers
-  static constexpr int STG_STRIDE = 36;    // floats per thread in the staging chunk (16-B aligned, conflict-free)
-  // shared memory: [0,1024) emission tables (at a 512-aligned address inside), mbarriers,
-  // partial sums, timeout flag, raw-row ring, rotated rows, store/load staging
-  static constexpr int BAR_OFF = 1024;
-  static constexpr int PART_OFF = BAR_OFF + kRing * 8;
-  static constexpr int LOG_OFF = PART_OFF + 2 * TPW * W * 4;   // per-target log scale (double)
-  static constexpr int ST_OFF = LOG_OFF + TPW * 8;              // per-target status bits
+  static constexpr int STG_STRIDE = 36;    // floats per thread in the staging chunk (16-B aligned)
+  // shared memory: [0,768) emission tables (two 256-byte buffers at a 256-aligned address inside),
+  // mbarriers, partial sums, log ring, per-target log scale and status, timeout flag, TMA ring,
+  // store/load staging
+  static constexpr int BAR_OFF = 768;
+  static constexpr int PART_OFF = BAR_OFF + kSlots * 8;
+  static constexpr int LOGR_OFF = PART_OFF + 2 * TPW * W * 4;
+  static constexpr int LOG_OFF = ((LOGR_OFF + TPW * 32 * 4 + 7) / 8) * 8;
+  static constexpr int ST_OFF = LOG_OFF + TPW * 8;
   static constexpr int FLAG_OFF = ST_OFF + TPW * 4;
-  static constexpr int RAW_OFF = ((FLAG_OFF + 16 + 127) / 128) * 128;
-  __host__ __device__ static SmemLayout layout(int N, int row_words) {
+  static constexpr int RING_OFF = ((FLAG_OFF + 16 + 127) / 128) * 128;
+  __host__ __device__ static SmemLayout layout(int rw2) {
     SmemLayout s;
-    s.nrot = (N + J + 31) / 32 + 2;
-    s.raw_off = RAW_OFF;
-    s.rot_off = RAW_OFF + round_up(kRing * row_words * 4, 128);
-    s.stg_off = s.rot_off + round_up(2 * s.nrot * 4, 128);
+    s.ring_off = RING_OFF;
+    s.stg_off = RING_OFF + round_up(kSlots * kRB * rw2 * 4, 128);
     s.total = s.stg_off + THREADS * STG_STRIDE * 4;
     return s;
+  }
+  // a variant serves N when a slice fits the slots and only a slice's last word is partial
+  __host__ static bool serves(int N) {
+    const int Jr = (N + S - 1) / S;
+    return Jr >= TPW && Jr <= J && (NWORD == 1 || Jr - 1 >= 32 * (NWORD - 1));
   }
 };
 
 // Slice geometry: S slices over N rotated positions; slice sigma has len positions starting at
 // start; the last mshort slices are one shorter.
-__device__ __forceinline__ void slice_of(int sigma, int S, int N, int& start, int& len) {
+__host__ __device__ __forceinline__ void slice_of(int sigma, int S, int N, int& start, int& len) {
   const int Jr = (N + S - 1) / S;
   const int mshort = S * Jr - N;
   len = Jr - (sigma >= S - mshort ? 1 : 0);
   start = sigma * Jr - (sigma > S - mshort ? sigma - (S - mshort) : 0);
 }
 
-template <int TPW, int W, int KQ>
+template <int DIR, int TPW, int W, int KQ>
 __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) {
   using C = PropCfg<TPW, W, KQ>;
   constexpr int SPW = C::SPW, S = C::S, NWORD = C::NWORD, THREADS = C::THREADS;
+  constexpr int step_dir = DIR == 0 ? 1 : -1;
   extern __shared__ __align__(128) unsigned char smem[];
   const int N = p.N;
-  const SmemLayout lay = C::layout(N, p.row_words);
+  const int rw2 = p.rw2;
+  const SmemLayout lay = C::layout(rw2);
   float* part = reinterpret_cast<float*>(smem + C::PART_OFF);
+  float* lgr = reinterpret_cast<float*>(smem + C::LOGR_OFF);
+  double* lgs = reinterpret_cast<double*>(smem + C::LOG_OFF);
+  uint32_t* sts = reinterpret_cast<uint32_t*>(smem + C::ST_OFF);
   volatile int* flag = reinterpret_cast<volatile int*>(smem + C::FLAG_OFF);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
   const uint32_t smem_base = smem_u32(smem);
-  float* lutf = reinterpret_cast<float*>(smem + (((smem_base + 511u) & ~511u) - smem_base));
-  uint32_t* raw = reinterpret_cast<uint32_t*>(smem + lay.raw_off);
-  uint32_t* rot = reinterpret_cast<uint32_t*>(smem + lay.rot_off);
+  const uint32_t lut_addr = (smem_base + 255u) & ~255u;  // low byte 0: PRMT builds full addresses
+  float* lutf = reinterpret_cast<float*>(smem + (lut_addr - smem_base));
+  uint32_t* ring = reinterpret_cast<uint32_t*>(smem + lay.ring_off);
   float* stg = reinterpret_cast<float*>(smem + lay.stg_off);
-  const int nrot = lay.nrot;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -247,13 +258,14 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
   const int o = p.t_begin + blockIdx.x * TPW;  // first target of this CTA (< N)
   int start, len;
   slice_of(warp * SPW + sl, S, N, start, len);
-  const int wbase = start >> 5;
-  const uint32_t wshift = (uint32_t)(start & 31);
+  const int b0 = start + o;                     // first bit of this lane's slice in a doubled row
+  const int wb = b0 >> 5;
+  const uint32_t wsh = (uint32_t)(b0 & 31);
+  const int abit = o + tl;                      // bit of the target itself
   const float n_junk = (float)(S * C::J - (N - 1));
-  // the diagonal of target tl is rotated position tl = slot tl of slice 0 (host: slice 0 >= TPW)
-  const uint32_t dclear = (warp == 0 && sl == 0) ? ~(1u << tl) : 0xffffffffu;
-  const int step_dir = p.dir == 0 ? 1 : -1;
-  const uint32_t row_bytes = (uint32_t)p.row_words * 4u;
+  const uint32_t dclear = (warp == 0 && sl == 0) ? ~(1u << tl) : 0xffffffffu;  // diagonal = slot tl of slice 0
+  const int vl = len - 32 * (NWORD - 1);        // valid slots of the last word
+  const uint32_t vmask_last = vl >= 32 ? 0xffffffffu : (vl <= 0 ? 0u : ((1u << vl) - 1u));
 
   // ---- staged transfers between the register tile and global memory (store loci only) ------
   // element (src thread, slot s of chunk c) <-> donor (start_src + 32c + s + o) mod N of target
@@ -286,36 +298,35 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     }
   };
 
-  // ---- prologue: barriers, first TMA copies, rotated row and emission table of step 0 --------
+  // ---- TMA blocks of kRB consecutive rows ------------------------------------------------------
+  auto blk_rows = [&](int B, int& base, int& nrows) {
+    nrows = min(kRB, p.n_steps - kRB * B);
+    base = DIR == 0 ? p.l_first + kRB * B : p.l_first - kRB * B - (nrows - 1);
+  };
+  auto issue = [&](int B) {
+    int base, nrows;
+    blk_rows(B, base, nrows);
+    tma_row(ring + (B % kSlots) * kRB * rw2, p.bits2 + (size_t)base * rw2, (uint32_t)(nrows * rw2 * 4), &bars[B % kSlots]);
+  };
+  const int nblk = (p.n_steps + kRB - 1) / kRB;
+
   if (tid == 0) {
     *flag = 0;
-    for (int s = 0; s < kRing; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < kSlots; ++s) mbar_init(&bars[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
-  if (tid == 0) {
-    for (int s = 0; s < kRing && s < p.n_steps; ++s) {
-      const int l = p.l_first + step_dir * s;
-      tma_row(raw + s * p.row_words, p.bits + (size_t)l * p.row_words, row_bytes, &bars[s]);
-    }
+  // emission table of step 0 (for scalar mu it serves every step)
+  if (tid < 64) {
+    const int e = tid >> 2, k = tid & 3;
+    lutf[tid] = ((e >> k) & 1) ? p.thm[p.l_first] : p.thx[p.l_first];
   }
-  auto build = [&](int step, int par) {
-    const int l = p.l_first + step_dir * step;
-    mbar_wait_bounded(&bars[step % kRing], (uint32_t)((step / kRing) & 1), flag);
-    const uint32_t* src = raw + (step % kRing) * p.row_words;
-    uint32_t* dst = rot + par * nrot;
-    for (int q = tid; q < nrot; q += THREADS) {
-      int g = 32 * q + o;
-      while (g >= N) g -= N;
-      dst[q] = N >= 32 ? cyclic32(src, N, g) : cyclic32_slow(src, N, g);
-    }
-    if (tid < 64) {
-      const int e = tid >> 2, k = tid & 3;
-      lutf[par * 64 + tid] = ((e >> k) & 1) ? p.thm[l] : p.thx[l];
-    }
-  };
-  build(0, 0);
+  if (tid < TPW) {
+    lgs[tid] = (o + tid < p.t_begin + p.t_count && p.logs && !p.init) ? p.logs[o + tid - p.tab_t0] : 0.0;
+    sts[tid] = 0u;
+  }
   __syncthreads();
+  if (tid == 0)
+    for (int B = 0; B < kSlots && B < nblk; ++B) issue(B);
 
   // ---- the register tile ------------------------------------------------------------------
   u64 x[KQ][2];
@@ -362,13 +373,6 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     }
   };
 
-  // per-target log scale and status live in shared memory, touched by threads tid < TPW only
-  double* lgs = reinterpret_cast<double*>(smem + C::LOG_OFF);
-  uint32_t* sts = reinterpret_cast<uint32_t*>(smem + C::ST_OFF);
-  if (tid < TPW) {
-    lgs[tid] = (o + tid < p.t_begin + p.t_count && p.logs && !p.init) ? p.logs[o + tid - p.tab_t0] : 0.0;
-    sts[tid] = 0u;
-  }
   float sig_prev = 1.0f;  // previous normaliser (fwd: sum alpha; bwd: S)
   float xs = 0.0f;        // common value of the junk cells
 
@@ -383,8 +387,29 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     for (int w = 0; w < W; ++w) t += buf[tl * W + w];
     return t;
   };
+  // fold the log ring into the FP64 log scales (warp 0; entries 0..cnt-1) and check the normalisers
+  auto flush_logs = [&](int cnt) {
+    if (warp != 0) return;
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < TPW; ++t) {
+      const float sg = lane < cnt ? lgr[t * 32 + lane] : 1.0f;
+      uint32_t stb = 0u;
+      if (sg < 1.17549435e-38f) stb |= 1u;      // LS_STATUS_UNDERFLOW: zero or subnormal normaliser
+      if (!(sg <= 3.40282347e+38f)) stb |= 2u;  // LS_STATUS_OVERFLOW: infinite or NaN normaliser
+      double v = (double)logf(sg);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      const uint32_t any = __reduce_or_sync(0xffffffffu, stb);
+      if (lane == 0) {
+        lgs[t] += v;
+        sts[t] |= any;
+      }
+    }
+    __syncwarp();
+  };
 
-  if (p.load_state && p.dir == 0) {
+  if (p.load_state && DIR == 0) {
     float s = 0.0f;
 #pragma unroll
     for (int k = 0; k < KQ; ++k) s += hsum2(x[k][0]) + hsum2(x[k][1]);
@@ -393,49 +418,55 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
   }
 
   // per-step scalars, loaded one step ahead
-  float nx_omr = 0.f, nx_rr = 0.f, nx_thx = p.thx[p.l_first];
+  float nx_omr = 0.f, nx_rr = 0.f, nx_thx = p.thx[p.l_first], nx_thm = p.thm[p.l_first];
   {
-    const int li = p.dir == 0 ? p.l_first - 1 : p.l_first;
+    const int li = DIR == 0 ? p.l_first - 1 : p.l_first;
     if (li >= 0 && li < p.L - 1) {
       nx_omr = p.omr[li];
       nx_rr = p.rr[li];
     }
   }
   int store_next = 0;
+  const uint32_t* slot_rows = ring;
+  int blk_base = 0, blk_n = 0;
   for (int step = 0; step < p.n_steps; ++step) {
-    const int par = step & 1;
     const int l = p.l_first + step_dir * step;
     const float cur_omr = nx_omr, cur_rr = nx_rr, cur_thx = nx_thx;
     if (step + 1 < p.n_steps) {
       const int ln = l + step_dir;
-      const int li = p.dir == 0 ? ln - 1 : ln;
+      const int li = DIR == 0 ? ln - 1 : ln;
       nx_omr = p.omr[li];
       nx_rr = p.rr[li];
       nx_thx = p.thx[ln];
+      nx_thm = p.thm[ln];
     }
-    // refill the ring slot freed by the previous step
-    if (tid == 0 && step + kRing < p.n_steps) {
-      const int s2 = step + kRing;
-      const int l2 = p.l_first + step_dir * s2;
-      tma_row(raw + (s2 % kRing) * p.row_words, p.bits + (size_t)l2 * p.row_words, row_bytes, &bars[s2 % kRing]);
+    const int j = step & (kRB - 1);
+    if (j == 0) {
+      const int B = step / kRB;
+      if (tid == 0 && B >= 1 && B + kSlots - 1 < nblk) issue(B + kSlots - 1);  // slot of block B-1 is free
+      mbar_wait_bounded(&bars[B % kSlots], (uint32_t)((B / kSlots) & 1), flag);
+      slot_rows = ring + (B % kSlots) * kRB * rw2;
+      blk_rows(B, blk_base, blk_n);
     }
+    const uint32_t* rw = slot_rows + (l - blk_base) * rw2;
+
     float c, r;
     bool add_log_prev = false;
     if (step == 0 && p.init) {
       c = 0.0f;
-      r = p.dir == 0 ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
-    } else if (step == 0 && p.dir == 1) {
+      r = DIR == 0 ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
+    } else if (step == 0 && DIR == 1) {
       c = 1.0f;  // backward resume: x = theta^l beta^l from the stored beta
       r = 0.0f;
     } else {
       c = __fdiv_rn(cur_omr, sig_prev);  // interval l-1 (fwd) or l (bwd)
       r = cur_rr;
-      add_log_prev = p.dir == 1;
+      add_log_prev = DIR == 1;
     }
     const bool is_store = store_next < p.n_store && p.store_loci[store_next] == l;
     const bool save_here = p.save_state && step == p.n_steps - 1;
 
-    if (p.dir == 1 && (is_store || save_here)) {
+    if (DIR == 1 && (is_store || save_here)) {
       // beta^l = c t^{l+1} + rho, the pre-emission value; when decoding, alpha^l beta^l
       // overwrites alpha^l in place (normalised by the decode kernel)
       const int slot = is_store ? p.store_slot[store_next] : 0;
@@ -445,27 +476,26 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     }
 
     // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
-    const uint32_t* rw = rot + par * nrot;
-    const uint32_t inv = ((rw[0] >> tl) & 1u) ? 0u : 0xffffffffu;  // target allele at l (position tl)
-    uint32_t wm[NWORD];
-#pragma unroll
-    for (int m = 0; m < NWORD; ++m) {
-      const int v = len - 32 * m;
-      const uint32_t vm = v >= 32 ? 0xffffffffu : (v <= 0 ? 0u : ((1u << v) - 1u));
-      uint32_t w = (funnel(rw[wbase + m], rw[wbase + m + 1], wshift) ^ inv) & vm;
-      if (m == 0) w &= dclear;
-      wm[m] = w;
-    }
-    const uint32_t lut_base = smem_u32(lutf + par * 64);
+    const uint32_t inv = ((rw[abit >> 5] >> (abit & 31)) & 1u) ? 0u : 0xffffffffu;  // target allele
+    const uint32_t lut_b = lut_addr + (p.mu_vec ? (uint32_t)((step & 1) << 8) : 0u);
     const u64 C2 = pk2(c, c), R2 = pk2(r, r);
     u64 acc0 = 0ull, acc1 = 0ull;
+    uint32_t hi16 = 0, lo16 = 0;
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
-      const uint32_t w = wm[k >> 3];
       const int q = k & 7;
-      const uint32_t off = q == 0 ? (w << 4) : (w >> (4 * q - 4));
+      if (q == 0) {
+        const int m = k >> 3;
+        uint32_t w = funnel(rw[wb + m], rw[wb + m + 1], wsh) ^ inv;  // match bits of 32 slots
+        if (m == NWORD - 1) w &= vmask_last;
+        if (m == 0) w &= dclear;
+        hi16 = w & 0xf0f0f0f0u;         // 16 x odd nibbles, one per byte
+        lo16 = (w << 4) & 0xf0f0f0f0u;  // 16 x even nibbles
+      }
+      // PRMT: byte q/2 of the nibble word as the low byte, table base in the upper bytes
+      const uint32_t addr = __byte_perm((q & 1) ? hi16 : lo16, lut_b, 0x7650u | (uint32_t)(q >> 1));
       u64 th01, th23;
-      lds128((off & 0xf0u) | lut_base, th01, th23);
+      lds128(addr, th01, th23);
       const u64 u01 = ffma2(C2, x[k][0], R2);
       const u64 u23 = ffma2(C2, x[k][1], R2);
       x[k][0] = fmul2(th01, u01);
@@ -475,25 +505,23 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     }
     xs = cur_thx * fmaf(c, xs, r);  // junk cells: theta = mu in every lane
 
-    if (p.dir == 0 && (is_store || save_here)) {
+    if (DIR == 0 && (is_store || save_here)) {
       if (is_store && p.store) store_tile(p.store + (size_t)p.store_slot[store_next] * p.state_rows * N, 0, 0.f, 0.f);
       if (save_here) store_tile(p.state, 0, 0.f, 0.f);
     }
     if (is_store) ++store_next;
 
-    if (step + 1 < p.n_steps) build(step + 1, par ^ 1);  // stage the next locus
-
-    const float tot = reduce(hsum2(acc0) + hsum2(acc1), part + par * TPW * W);
-    float sig = tot - n_junk * xs;
-    if (p.dir == 1) sig *= p.pi_u;
-    if (tid < TPW) {
-      uint32_t stb = 0u;
-      if (sig < 1.17549435e-38f) stb |= 1u;        // LS_STATUS_UNDERFLOW: zero or subnormal normaliser
-      if (!(sig <= 3.40282347e+38f)) stb |= 2u;    // LS_STATUS_OVERFLOW: infinite or NaN normaliser
-      if (stb) sts[tid] |= stb;
-      if (p.dir == 0) lgs[tid] += (double)logf(sig);
-      else if (add_log_prev) lgs[tid] += (double)logf(sig_prev);
+    // emission table of the next locus (mu varying per locus), into the other buffer
+    if (p.mu_vec && tid < 64 && step + 1 < p.n_steps) {
+      const int e = tid >> 2, k = tid & 3;
+      lutf[((step + 1) & 1) * 64 + tid] = ((e >> k) & 1) ? nx_thm : nx_thx;
     }
+
+    const float tot = reduce(hsum2(acc0) + hsum2(acc1), part + (step & 1) * TPW * W);
+    float sig = tot - n_junk * xs;
+    if (DIR == 1) sig *= p.pi_u;
+    if (tid < TPW) lgr[tid * 32 + (step & 31)] = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
+    if ((step & 31) == 31 || step == p.n_steps - 1) flush_logs((step & 31) + 1);
     sig_prev = sig;
   }
 
