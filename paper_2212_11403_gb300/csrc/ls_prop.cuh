@@ -71,44 +71,10 @@ struct PropParams {
 };
 
 typedef unsigned long long u64;
+typedef float2 f2;
 
-__device__ __forceinline__ u64 pk2(float a, float b) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void up2(u64 v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ float hsum2(u64 v) {
-  float a, b;
-  up2(v, a, b);
-  return a + b;
-}
-// Keeps the compiler from hoisting the memory operations of one quad above the previous quad's
-// (the store passes run only at store loci; without this their unrolled loads stay live at once).
-__device__ __forceinline__ void quad_fence() { asm volatile("" ::: "memory"); }
-__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
-  u64 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
-  u64 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
-  u64 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-// 16-byte shared load as two f32x2 pairs (not volatile: the compiler may hoist it ahead of use)
-__device__ __forceinline__ void lds128(uint32_t addr, u64& a, u64& b) {
-  asm("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }
 __device__ __forceinline__ uint32_t funnel(uint32_t lo, uint32_t hi, uint32_t s) {
   return __funnelshift_r(lo, hi, s);  // (hi:lo) >> s, s in [0, 31]
@@ -197,10 +163,9 @@ struct PropCfg {
   static constexpr int NCHUNK = (KQ + 7) / 8;  // 8-quad chunks staged through shared memory
   static constexpr int THREADS = W * 32;
   static constexpr int STG_STRIDE = 36;    // floats per thread in the staging chunk (16-B aligned)
-  // shared memory: [0,768) emission tables (two 256-byte buffers at a 256-aligned address inside),
-  // mbarriers, partial sums, log ring, per-target log scale and status, timeout flag, TMA ring,
-  // store/load staging
-  static constexpr int BAR_OFF = 768;
+  // dynamic shared memory: mbarriers, partial sums, log ring, per-target log scale and status,
+  // timeout flag, TMA ring, store/load staging (the emission tables are static shared memory)
+  static constexpr int BAR_OFF = 0;
   static constexpr int PART_OFF = BAR_OFF + kSlots * 8;
   static constexpr int LOGR_OFF = PART_OFF + 2 * TPW * W * 4;
   static constexpr int LOG_OFF = ((LOGR_OFF + TPW * 32 * 4 + 7) / 8) * 8;
@@ -245,9 +210,10 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
   uint32_t* sts = reinterpret_cast<uint32_t*>(smem + C::ST_OFF);
   volatile int* flag = reinterpret_cast<volatile int*>(smem + C::FLAG_OFF);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
-  const uint32_t smem_base = smem_u32(smem);
-  const uint32_t lut_addr = (smem_base + 255u) & ~255u;  // low byte 0: PRMT builds full addresses
-  float* lutf = reinterpret_cast<float*>(smem + (lut_addr - smem_base));
+  // emission tables: two 256-byte buffers (this step's and the next one's when mu varies per locus),
+  // indexed by 16 x (4 match bits); static so the table's address folds into the load offset
+  __shared__ __align__(256) float s_lut[2][64];
+  float* lutf = &s_lut[0][0];
   uint32_t* ring = reinterpret_cast<uint32_t*>(smem + lay.ring_off);
   float* stg = reinterpret_cast<float*>(smem + lay.stg_off);
 
@@ -329,9 +295,9 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     for (int B = 0; B < kSlots && B < nblk; ++B) issue(B);
 
   // ---- the register tile ------------------------------------------------------------------
-  u64 x[KQ][2];
+  f2 x[KQ][2];
 #pragma unroll
-  for (int k = 0; k < KQ; ++k) x[k][0] = x[k][1] = 0ull;
+  for (int k = 0; k < KQ; ++k) x[k][0] = x[k][1] = make_float2(0.f, 0.f);
   if (p.load_state) {
 #pragma unroll
     for (int c = 0; c < C::NCHUNK; ++c) {
@@ -341,9 +307,9 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
       for (int q = 0; q < 8; ++q) {
         const int k = 8 * c + q;
         if (k < KQ) {
-          const float* sp = stg + tid * C::STG_STRIDE + 4 * q;
-          x[k][0] = pk2(sp[0], sp[1]);
-          x[k][1] = pk2(sp[2], sp[3]);
+          const float4 v = *reinterpret_cast<const float4*>(stg + tid * C::STG_STRIDE + 4 * q);
+          x[k][0] = make_float2(v.x, v.y);
+          x[k][1] = make_float2(v.z, v.w);
         }
       }
       __syncthreads();
@@ -351,20 +317,16 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
   }
   // store the tile (mode 0: x; 1: c x + r; 2: multiply the destination by c x + r)
   auto store_tile = [&](float* gbase, int mode, float c, float r) {
-    const u64 C2 = pk2(c, c), R2 = pk2(r, r);
+    const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
 #pragma unroll
     for (int cc = 0; cc < C::NCHUNK; ++cc) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int k = 8 * cc + q;
         if (k < KQ) {
-          const u64 a = mode == 0 ? x[k][0] : ffma2(C2, x[k][0], R2);
-          const u64 b = mode == 0 ? x[k][1] : ffma2(C2, x[k][1], R2);
-          float* sp = stg + tid * C::STG_STRIDE + 4 * q;
-          float v0, v1, v2, v3;
-          up2(a, v0, v1);
-          up2(b, v2, v3);
-          *reinterpret_cast<float4*>(sp) = make_float4(v0, v1, v2, v3);
+          const f2 a = mode == 0 ? x[k][0] : __ffma2_rn(C2, x[k][0], R2);
+          const f2 b = mode == 0 ? x[k][1] : __ffma2_rn(C2, x[k][1], R2);
+          *reinterpret_cast<float4*>(stg + tid * C::STG_STRIDE + 4 * q) = make_float4(a.x, a.y, b.x, b.y);
         }
       }
       __syncthreads();
@@ -412,7 +374,7 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
   if (p.load_state && DIR == 0) {
     float s = 0.0f;
 #pragma unroll
-    for (int k = 0; k < KQ; ++k) s += hsum2(x[k][0]) + hsum2(x[k][1]);
+    for (int k = 0; k < KQ; ++k) s += (x[k][0].x + x[k][0].y) + (x[k][1].x + x[k][1].y);
     sig_prev = reduce(s, part + TPW * W);
     __syncthreads();
   }
@@ -427,6 +389,9 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     }
   }
   int store_next = 0;
+  int next_store_l = p.n_store > 0 ? p.store_loci[0] : -1;  // next locus with a store (-1: none)
+  int pend_slot = -1;     // forward: store slot of the previous locus' alpha, written next step
+  bool pend_save = false; // forward: save the state after the last step
   const uint32_t* slot_rows = ring;
   int blk_base = 0, blk_n = 0;
   for (int step = 0; step < p.n_steps; ++step) {
@@ -459,12 +424,16 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
       c = 1.0f;  // backward resume: x = theta^l beta^l from the stored beta
       r = 0.0f;
     } else {
-      c = __fdiv_rn(cur_omr, sig_prev);  // interval l-1 (fwd) or l (bwd)
+      c = __fdividef(cur_omr, sig_prev);  // interval l-1 (fwd) or l (bwd); 2-ulp reciprocal-multiply
       r = cur_rr;
       add_log_prev = DIR == 1;
     }
-    const bool is_store = store_next < p.n_store && p.store_loci[store_next] == l;
+    const bool is_store = l == next_store_l;
     const bool save_here = p.save_state && step == p.n_steps - 1;
+    if (DIR == 0 && pend_slot >= 0) {  // alpha of the previous locus
+      store_tile(p.store + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f);
+      pend_slot = -1;
+    }
 
     if (DIR == 1 && (is_store || save_here)) {
       // beta^l = c t^{l+1} + rho, the pre-emission value; when decoding, alpha^l beta^l
@@ -477,39 +446,55 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
 
     // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
     const uint32_t inv = ((rw[abit >> 5] >> (abit & 31)) & 1u) ? 0u : 0xffffffffu;  // target allele
-    const uint32_t lut_b = lut_addr + (p.mu_vec ? (uint32_t)((step & 1) << 8) : 0u);
-    const u64 C2 = pk2(c, c), R2 = pk2(r, r);
-    u64 acc0 = 0ull, acc1 = 0ull;
-    uint32_t hi16 = 0, lo16 = 0;
+    const uint32_t lut_b = p.mu_vec ? (uint32_t)((step & 1) << 8) : 0u;  // byte offset of this step's table
+    const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
+    f2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    // Software pipeline: the emission-table entries are loaded kLA quads ahead of their use from a
+    // rotating register buffer; a slice word's nibbles are prepared when the lookahead enters it.
+    constexpr int kLA = KQ < 4 ? KQ : 4;
+    uint32_t hw[2], lw[2];   // 16 x nibble bytes of the words feeding the lookahead (double-buffered)
+    float4 th[kLA];
+    auto prep_word = [&](int m) {
+      uint32_t w = funnel(rw[wb + m], rw[wb + m + 1], wsh) ^ inv;  // match bits of 32 slots
+      if (m == NWORD - 1) w &= vmask_last;
+      if (m == 0) w &= dclear;
+      hw[m & 1] = w & 0xf0f0f0f0u;         // 16 x odd nibbles, one per byte
+      lw[m & 1] = (w << 4) & 0xf0f0f0f0u;  // 16 x even nibbles
+    };
+    auto load_th = [&](int kk) -> float4 {
+      const int q = kk & 7, m = kk >> 3;
+      // PRMT: byte q/2 of the nibble word as the low byte, the table's buffer offset above it
+      const uint32_t off = __byte_perm((q & 1) ? hw[m & 1] : lw[m & 1], lut_b, 0x7650u | (uint32_t)(q >> 1));
+      return *reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(s_lut) + off);
+    };
+    prep_word(0);
+#pragma unroll
+    for (int k = 0; k < kLA; ++k) th[k] = load_th(k);
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
-      const int q = k & 7;
-      if (q == 0) {
-        const int m = k >> 3;
-        uint32_t w = funnel(rw[wb + m], rw[wb + m + 1], wsh) ^ inv;  // match bits of 32 slots
-        if (m == NWORD - 1) w &= vmask_last;
-        if (m == 0) w &= dclear;
-        hi16 = w & 0xf0f0f0f0u;         // 16 x odd nibbles, one per byte
-        lo16 = (w << 4) & 0xf0f0f0f0u;  // 16 x even nibbles
+      const float4 t = th[k % kLA];
+      const int kn = k + kLA;
+      if (kn < KQ) {
+        if ((kn & 7) == 0) prep_word(kn >> 3);
+        th[k % kLA] = load_th(kn);
       }
-      // PRMT: byte q/2 of the nibble word as the low byte, table base in the upper bytes
-      const uint32_t addr = __byte_perm((q & 1) ? hi16 : lo16, lut_b, 0x7650u | (uint32_t)(q >> 1));
-      u64 th01, th23;
-      lds128(addr, th01, th23);
-      const u64 u01 = ffma2(C2, x[k][0], R2);
-      const u64 u23 = ffma2(C2, x[k][1], R2);
-      x[k][0] = fmul2(th01, u01);
-      x[k][1] = fmul2(th23, u23);
-      acc0 = fadd2(acc0, x[k][0]);
-      acc1 = fadd2(acc1, x[k][1]);
+      const f2 u01 = __ffma2_rn(C2, x[k][0], R2);
+      const f2 u23 = __ffma2_rn(C2, x[k][1], R2);
+      x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
+      x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
+      acc0 = __fadd2_rn(acc0, x[k][0]);
+      acc1 = __fadd2_rn(acc1, x[k][1]);
     }
     xs = cur_thx * fmaf(c, xs, r);  // junk cells: theta = mu in every lane
 
-    if (DIR == 0 && (is_store || save_here)) {
-      if (is_store && p.store) store_tile(p.store + (size_t)p.store_slot[store_next] * p.state_rows * N, 0, 0.f, 0.f);
-      if (save_here) store_tile(p.state, 0, 0.f, 0.f);
+    if (DIR == 0) {  // alpha^l is stored at the top of the next step (or after the loop)
+      pend_slot = is_store && p.store ? p.store_slot[store_next] : -1;
+      pend_save = save_here;
     }
-    if (is_store) ++store_next;
+    if (is_store) {
+      ++store_next;
+      next_store_l = store_next < p.n_store ? p.store_loci[store_next] : -1;
+    }
 
     // emission table of the next locus (mu varying per locus), into the other buffer
     if (p.mu_vec && tid < 64 && step + 1 < p.n_steps) {
@@ -517,7 +502,7 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
       lutf[((step + 1) & 1) * 64 + tid] = ((e >> k) & 1) ? nx_thm : nx_thx;
     }
 
-    const float tot = reduce(hsum2(acc0) + hsum2(acc1), part + (step & 1) * TPW * W);
+    const float tot = reduce((acc0.x + acc0.y) + (acc1.x + acc1.y), part + (step & 1) * TPW * W);
     float sig = tot - n_junk * xs;
     if (DIR == 1) sig *= p.pi_u;
     if (tid < TPW) lgr[tid * 32 + (step & 31)] = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
@@ -525,6 +510,10 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     sig_prev = sig;
   }
 
+  if (DIR == 0) {
+    if (pend_slot >= 0) store_tile(p.store + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f);
+    if (pend_save) store_tile(p.state, 0, 0.f, 0.f);
+  }
   if (tid < TPW && o + tid < p.t_begin + p.t_count) {
     const int row = o + tid - p.tab_t0;
     const uint32_t stb = sts[tid] | (*flag ? 4u : 0u);  // 4 = LS_STATUS_TIMEOUT
