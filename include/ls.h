@@ -167,6 +167,31 @@ int ls_distance(ls_ctx* ctx, const ls_table* fwd, const ls_table* bck, float* d_
 int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out, double* pac_out,
                uint32_t* status_out, ls_stream_t stream);
 
+/* ---- fused pipeline without allocation --------------------------------------------------- */
+
+/* Largest N the allocation-free pipeline accepts: its scratch is a fixed area inside the library
+ * sized for this many targets (LS_NOALLOC_MAX_N x 12 bytes plus a few words, about 768 KB, held
+ * by every GPU that loads the library until the process exits). */
+#define LS_NOALLOC_MAX_N 65536
+
+/* The paper has no counterpart to this entry point.  Same computation as ls_run_all (forward and
+ * backward over all loci, posterior and symmetrised distances at the D decode loci, the PAC
+ * log-likelihood) for callers that must not allocate device memory while they run it: code that
+ * is being captured into a CUDA graph (cudaMalloc is not allowed during stream capture), code
+ * that lives inside a framework or serving loop owning a fixed device-memory budget, and code for
+ * which cudaMalloc's implicit device synchronisation is unacceptable.  It allocates nothing: the
+ * caller passes d_out (device float [D][N][N], required, no host buffer) and the optional outputs
+ * as for ls_run_all; per-target log scales, status words, the error word and the PAC sum live in
+ * the library's fixed scratch area.  The first call on each device looks up that area's device
+ * address (cudaGetSymbolAddress) with the context's device current, so make the first call before
+ * any stream capture.  All calls share the one area and reuse it: the call clears what must start
+ * at zero, and calls whose GPU work overlaps (different streams, or different contexts on one
+ * device running at once) race on it.  N > LS_NOALLOC_MAX_N gives LS_ERR_UNSUPPORTED; D is limited
+ * to 64 as for ls_run_all.  Synchronous when pac_out is given (it waits for the PAC sum and
+ * returns LS_WARN_* like ls_run_all), asynchronous otherwise. */
+int ls_run_all_noalloc(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out, double* pac_out,
+                       uint32_t* status_out, ls_stream_t stream);
+
 /* ---- profiling (tracing hook) ------------------------------------------------------------ */
 
 /* Enable (1) or disable (0) phase timing of ls_run_all on this context.  When enabled, each

@@ -791,3 +791,205 @@ int ls_profile_read(ls_ctx* ctx, float* ms, int32_t* launches) {
 }
 
 }  // extern "C"
+
+// ---- the allocation-free pipeline -----------------------------------------------------------
+// Its scratch lives in a file-scope device array (every GPU that loads the library holds it until
+// exit).  Host code must never hand the symbol itself to a kernel: in host code the name is a
+// stand-in, not a device address.  The address is looked up once per device.
+namespace {
+
+struct NoallocScratch {
+  double logF[LS_NOALLOC_MAX_N];    // per-target log F at the last locus
+  uint32_t status[LS_NOALLOC_MAX_N];
+  double pac;                       // PAC log-likelihood
+  uint32_t any;                     // OR of the status words
+  int err;                          // device error word (timed-out waits)
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoallocScratch* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch area for the current device (looked up on first use).
+int noalloc_scratch(int device, NoallocScratch** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(LS_ERR_UNSUPPORTED, "device %d beyond %d", device, kMaxDevices);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return fail(LS_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_ptr[device] = static_cast<NoallocScratch*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return LS_OK;
+}
+
+// PAC = sum_i log F_i in a fixed order (one CTA, strided partial sums, then a fixed tree), and
+// the OR of the status words.
+__global__ void pac_reduce_kernel(const double* __restrict__ logF, const uint32_t* __restrict__ status, int N,
+                                  double* __restrict__ pac, uint32_t* __restrict__ any) {
+  __shared__ double sd[256];
+  __shared__ uint32_t su[256];
+  double s = 0.0;
+  uint32_t u = 0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    s += logF[i];
+    u |= status[i];
+  }
+  sd[threadIdx.x] = s;
+  su[threadIdx.x] = u;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sd[threadIdx.x] += sd[threadIdx.x + w];
+      su[threadIdx.x] |= su[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *pac = sd[0];
+    *any = su[0];
+  }
+}
+
+// Launch plan with fixed-size arrays (no heap use on this path).
+int plan_fixed(ls_ctx* c, int t_count, Launch* out, int* nout) {
+  struct C2 {
+    const PropKernelInfo* k;
+    int smem, per_sm;
+  };
+  C2 cs[64];
+  int nc = 0;
+  for (const auto& k : registry()) {
+    if (nc >= 64) break;
+    if (!k.serves(c->N)) continue;
+    const int smem = k.smem_bytes(c->rw2);
+    if (smem > 227 * 1024) continue;
+    bool ok = true;
+    for (int d = 0; d < 2 && ok; ++d)
+      if (cudaFuncSetAttribute(k.func[d], cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) ok = false;
+    int nb = 0;
+    if (ok && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.func[0], k.w * 32, smem) != cudaSuccess || nb < 1)) ok = false;
+    if (!ok) {
+      cudaGetLastError();
+      continue;
+    }
+    cs[nc++] = C2{&k, smem, nb};
+  }
+  if (!nc) return fail(LS_ERR_UNSUPPORTED, "no compiled propagation variant serves N=%d", c->N);
+  auto best = [&](int count, double* cost) {
+    int bi = 0;
+    double bc = 1e300;
+    for (int i = 0; i < nc; ++i) {
+      const double cc = cost_of(Cand{cs[i].k, cs[i].smem, cs[i].per_sm}, count, c->num_sms);
+      if (cc < bc * 0.999 || (cc <= bc * 1.001 && cs[i].k->tpw > cs[bi].k->tpw)) {
+        bc = cc;
+        bi = i;
+      }
+    }
+    *cost = bc;
+    return bi;
+  };
+  double c1 = 0, cm = 0, ct = 0;
+  const int b1 = best(t_count, &c1);
+  const int per_wave_t = c->num_sms * cs[b1].per_sm * cs[b1].k->tpw;
+  *nout = 0;
+  if (t_count > per_wave_t && t_count % per_wave_t != 0) {
+    const int main_t = (t_count / per_wave_t) * per_wave_t;
+    cm = cost_of(Cand{cs[b1].k, cs[b1].smem, cs[b1].per_sm}, main_t, c->num_sms);
+    const int bt = best(t_count - main_t, &ct);
+    if (cm + ct < c1) {
+      const int tt = t_count - main_t;
+      out[0] = Launch{cs[b1].k, 0, main_t, main_t / cs[b1].k->tpw, cs[b1].smem};
+      out[1] = Launch{cs[bt].k, main_t, tt, (tt + cs[bt].k->tpw - 1) / cs[bt].k->tpw, cs[bt].smem};
+      *nout = 2;
+      return LS_OK;
+    }
+  }
+  out[0] = Launch{cs[b1].k, 0, t_count, (t_count + cs[b1].k->tpw - 1) / cs[b1].k->tpw, cs[b1].smem};
+  *nout = 1;
+  return LS_OK;
+}
+
+}  // namespace
+
+extern "C" int ls_run_all_noalloc(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out, double* pac_out,
+                                  uint32_t* status_out, ls_stream_t stream) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
+  if (ctx->Pi) return fail(LS_ERR_UNSUPPORTED, "propagation with a prior matrix is not built yet (uniform prior only)");
+  const int N = ctx->N, L = ctx->L;
+  if (N > LS_NOALLOC_MAX_N)
+    return fail(LS_ERR_UNSUPPORTED, "ls_run_all_noalloc: N=%d exceeds its fixed scratch (LS_NOALLOC_MAX_N=%d targets)", N,
+                LS_NOALLOC_MAX_N);
+  if (D < 0 || (D > 0 && (!decode_loci || !d_out))) return fail(LS_ERR_ARG, "bad decode arguments");
+  if (D > lsk::kMaxStore) return fail(LS_ERR_UNSUPPORTED, "at most %d decode loci per call", lsk::kMaxStore);
+  for (int k = 0; k < D; ++k) {
+    if (decode_loci[k] < 0 || decode_loci[k] >= L) return fail(LS_ERR_ARG, "decode locus %d out of range", decode_loci[k]);
+    if (k && decode_loci[k] <= decode_loci[k - 1]) return fail(LS_ERR_ARG, "decode loci must be strictly increasing");
+  }
+  if (D > 0 && !is_device_ptr(d_out)) return fail(LS_ERR_ARG, "ls_run_all_noalloc needs d_out in device memory");
+  NoallocScratch* sc = nullptr;
+  if ((rc = noalloc_scratch(ctx->device, &sc))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // what must start at zero: the status words and the error word (log F is written in full)
+  CUDA_TRY(cudaMemsetAsync(sc->status, 0, sizeof(uint32_t) * N, s));
+  CUDA_TRY(cudaMemsetAsync(&sc->err, 0, sizeof(int), s));
+  Launch lp[2];
+  int nl = 0;
+  if ((rc = plan_fixed(ctx, N, lp, &nl))) return rc;
+  for (int dir = 0; dir < 2; ++dir) {
+    lsk::PropParams p;
+    base_params(ctx, p, dir);
+    p.err = &sc->err;
+    p.l_first = dir == 0 ? 0 : L - 1;
+    p.n_steps = L;
+    p.init = 1;
+    p.tab_t0 = 0;
+    p.state_rows = N;
+    p.status = sc->status;
+    p.n_store = D;
+    for (int k = 0; k < D; ++k) {
+      p.store_loci[k] = dir == 0 ? decode_loci[k] : decode_loci[D - 1 - k];
+      p.store_slot[k] = dir == 0 ? k : D - 1 - k;
+    }
+    if (dir == 0) {
+      p.logs = sc->logF;
+      p.store = d_out;
+    } else {
+      p.alpha_dec = d_out;
+    }
+    for (int i = 0; i < nl; ++i) {
+      p.t_begin = lp[i].t_begin;
+      p.t_count = lp[i].t_count;
+      cudaError_t e = lp[i].k->launch(dir, p, lp[i].grid, lp[i].smem, s);
+      if (e != cudaSuccess) return fail(LS_ERR_CUDA, "propagation launch: %s", cudaGetErrorString(e));
+    }
+  }
+  if (D > 0) {
+    lsk::decode_kernel<<<dim3(N, D), 256, 0, s>>>(d_out, N);
+    CUDA_TRY(cudaGetLastError());
+    const int nt = (N + 31) / 32;
+    lsk::symmetrize_kernel<<<dim3(nt, nt, D), dim3(32, 8), 0, s>>>(d_out, N);
+    CUDA_TRY(cudaGetLastError());
+  }
+  pac_reduce_kernel<<<1, 256, 0, s>>>(sc->logF, sc->status, N, &sc->pac, &sc->any);
+  CUDA_TRY(cudaGetLastError());
+  if (status_out) CUDA_TRY(cudaMemcpyAsync(status_out, sc->status, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
+  if (!pac_out) return LS_OK;
+  double pac = 0.0;
+  uint32_t any = 0;
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&pac, &sc->pac, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&any, &sc->any, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&err, &sc->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (err) return fail(LS_ERR_DEVICE, "a device wait for staged haplotype rows ran out of time");
+  *pac_out = pac;
+  if (any & 1u) return LS_WARN_UNDERFLOW;
+  if (any & 2u) return LS_WARN_OVERFLOW;
+  return LS_OK;
+}

@@ -33,12 +33,13 @@ LS_STATUS_OVERFLOW = 2
 LS_STATUS_TIMEOUT = 4
 LS_FWD = 0
 LS_BWD = 1
+LS_NOALLOC_MAX_N = 65536
 
 EXPORTED = [
     "ls_version", "ls_last_error", "ls_create", "ls_create_packed", "ls_destroy", "ls_info", "ls_query",
     "ls_export_packed", "ls_calc_rho", "ls_set_params", "ls_table_create", "ls_table_destroy", "ls_table_copy",
     "ls_table_reset", "ls_table_info", "ls_table_read", "ls_forward", "ls_backward", "ls_posterior", "ls_distance",
-    "ls_run_all", "ls_set_profiling", "ls_profile_read",
+    "ls_run_all", "ls_run_all_noalloc", "ls_set_profiling", "ls_profile_read",
 ]
 
 
@@ -76,6 +77,7 @@ def _load():
         "ls_posterior": ([P, P, P, P, P], I),
         "ls_distance": ([P, P, P, P, P], I),
         "ls_run_all": ([P, P, I, P, P, P, P], I),
+        "ls_run_all_noalloc": ([P, P, I, P, P, P, P], I),
         "ls_set_profiling": ([P, I], I),
         "ls_profile_read": ([P, P, P], I),
     }
@@ -256,6 +258,17 @@ def ls_run_all(ctx, decode_loci, d_out, want_pac=True, status_out=None, stream=N
     rc = _check(_lib.ls_run_all(ctx, dl.ctypes.data_as(ctypes.c_void_p) if dl.size else None, dl.size, dp,
                                 ctypes.byref(pac) if want_pac else None, _dev(status_out, torch.int32, "status"),
                                 _stream(stream)))
+    return rc, (pac.value if want_pac else None)
+
+
+def ls_run_all_noalloc(ctx, decode_loci, d_out, want_pac=True, status_out=None, stream=None):
+    """The allocation-free pipeline: d_out must be a CUDA float32 tensor [D, N, N].  Returns (rc, pac)."""
+    import torch
+    dl = np.ascontiguousarray(decode_loci, dtype=np.int32)
+    pac = ctypes.c_double(0.0)
+    rc = _check(_lib.ls_run_all_noalloc(ctx, dl.ctypes.data_as(ctypes.c_void_p) if dl.size else None, dl.size,
+                                        _dev(d_out, torch.float32, "d_out"), ctypes.byref(pac) if want_pac else None,
+                                        _dev(status_out, torch.int32, "status"), _stream(stream)))
     return rc, (pac.value if want_pac else None)
 
 
