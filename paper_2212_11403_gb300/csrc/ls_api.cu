@@ -20,6 +20,8 @@ void ls_register_group2(std::vector<PropKernelInfo>& out);
 void ls_register_group3(std::vector<PropKernelInfo>& out);
 void ls_register_group4(std::vector<PropKernelInfo>& out);
 void ls_register_group5(std::vector<PropKernelInfo>& out);
+void ls_register_group6(std::vector<PropKernelInfo>& out);
+void ls_register_group7(std::vector<PropKernelInfo>& out);
 
 namespace {
 
@@ -51,6 +53,8 @@ std::vector<PropKernelInfo>& registry() {
     ls_register_group3(v);
     ls_register_group4(v);
     ls_register_group5(v);
+    ls_register_group6(v);
+    ls_register_group7(v);
   });
   return v;
 }
@@ -90,8 +94,9 @@ struct Cand {
 std::vector<Cand> candidates(ls_ctx* c) {
   std::vector<Cand> out;
   const int N = c->N;
+  const int pim = c->Pi ? 1 : 0;
   for (const auto& k : registry()) {
-    if (!k.serves(N)) continue;
+    if (k.pim != pim || !k.serves(N)) continue;
     const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;
     bool ok = true;
@@ -114,7 +119,8 @@ double cost_of(const Cand& cd, int count, int nsm) {
   const long long ctas = (count + cd.k->tpw - 1) / cd.k->tpw;
   const long long per_wave = (long long)nsm * cd.per_sm;
   const long long full = ctas / per_wave, rem = ctas % per_wave;
-  const double unit = cd.k->w * (cd.k->kq + 3.0);
+  // fewer than two warps per scheduler leave the dependent FP32 chain exposed: count it double
+  const double unit = cd.k->w * (cd.k->kq + 3.0) * (cd.per_sm * cd.k->w < 8 ? 2.0 : 1.0);
   double t = (double)full * cd.per_sm * unit;
   if (rem) t += (double)((rem + nsm - 1) / nsm) * unit;
   return t;
@@ -183,6 +189,8 @@ void base_params(ls_ctx* c, lsk::PropParams& p, int dir) {
   p.thm = c->thm;
   p.thx = c->thx;
   p.pi_u = c->pi_u;
+  p.Pi = c->Pi;
+  if (c->Pi && dir == 0) p.rr = c->rr_b;  // the matrix-prior kernel multiplies rho by pi_j itself
   p.err = c->err;
 }
 
@@ -551,7 +559,6 @@ static int propagate(ls_ctx* ctx, ls_table* tb, int dir, int32_t to, const int32
   if (!tb || tb->ctx != ctx) return fail(LS_ERR_ARG, "table does not belong to this context");
   if (tb->kind != (dir == 0 ? LS_FWD : LS_BWD)) return fail(LS_ERR_ARG, "wrong table kind for this direction");
   if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
-  if (ctx->Pi) return fail(LS_ERR_UNSUPPORTED, "propagation with a prior matrix is not built yet (uniform prior only)");
   const int L = ctx->L;
   if (to < 0 || to >= L) return fail(LS_ERR_ARG, "locus %d out of range [0, %d)", to, L);
   const bool init = tb->locus < 0;
@@ -667,7 +674,6 @@ int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out,
   int rc = check_ctx(ctx);
   if (rc) return rc;
   if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
-  if (ctx->Pi) return fail(LS_ERR_UNSUPPORTED, "propagation with a prior matrix is not built yet (uniform prior only)");
   const int N = ctx->N, L = ctx->L;
   if (D < 0 || (D > 0 && (!decode_loci || !d_out))) return fail(LS_ERR_ARG, "bad decode arguments");
   if (D > lsk::kMaxStore) return fail(LS_ERR_UNSUPPORTED, "at most %d decode loci per call", lsk::kMaxStore);
@@ -864,7 +870,7 @@ int plan_fixed(ls_ctx* c, int t_count, Launch* out, int* nout) {
   int nc = 0;
   for (const auto& k : registry()) {
     if (nc >= 64) break;
-    if (!k.serves(c->N)) continue;
+    if (k.pim != (c->Pi ? 1 : 0) || !k.serves(c->N)) continue;
     const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;
     bool ok = true;
@@ -920,7 +926,6 @@ extern "C" int ls_run_all_noalloc(ls_ctx* ctx, const int32_t* decode_loci, int32
   int rc = check_ctx(ctx);
   if (rc) return rc;
   if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
-  if (ctx->Pi) return fail(LS_ERR_UNSUPPORTED, "propagation with a prior matrix is not built yet (uniform prior only)");
   const int N = ctx->N, L = ctx->L;
   if (N > LS_NOALLOC_MAX_N)
     return fail(LS_ERR_UNSUPPORTED, "ls_run_all_noalloc: N=%d exceeds its fixed scratch (LS_NOALLOC_MAX_N=%d targets)", N,

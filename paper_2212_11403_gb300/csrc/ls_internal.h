@@ -12,6 +12,7 @@
 // (forward and backward instantiations).
 struct PropKernelInfo {
   int tpw, w, kq;
+  int pim;  // 1: prior-matrix variant
   const void* func[2];
   cudaError_t (*launch)(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s);
   int (*smem_bytes)(int rw2);

@@ -55,6 +55,7 @@ struct PropParams {
   const float* thx;       // [L] mu (mismatch)
   int mu_vec;             // 1: mu differs between loci (the emission table is rebuilt every locus)
   float pi_u;             // uniform prior 1/(N-1)
+  const float* Pi;        // prior matrix [N][N] recipient-major (matrix-prior variants only)
   float* state;           // [state_rows][N] table state (alpha or beta)
   double* logs;           // [state_rows] log F / log G (may be null)
   uint32_t* status;       // [state_rows] status bits (may be null)
@@ -149,6 +150,7 @@ __device__ __forceinline__ uint32_t cyclic32_slow(const uint32_t* raw, int N, in
 struct SmemLayout {
   int ring_off;  // byte offsets of the regions
   int stg_off;
+  int pi_off;    // prior values of each lane's slots (matrix prior only)
   int total;
 };
 
@@ -172,15 +174,17 @@ struct PropCfg {
   static constexpr int ST_OFF = LOG_OFF + TPW * 8;
   static constexpr int FLAG_OFF = ST_OFF + TPW * 4;
   static constexpr int RING_OFF = ((FLAG_OFF + 16 + 127) / 128) * 128;
-  __host__ __device__ static SmemLayout layout(int rw2) {
+  static constexpr int PI_STRIDE = J + 4;  // floats per thread in the prior region (conflict-free 16-B loads)
+  __host__ __device__ static SmemLayout layout(int rw2, int pim) {
     SmemLayout s;
     s.ring_off = RING_OFF;
     s.stg_off = RING_OFF + round_up(kSlots * kRB * rw2 * 4, 128);
-    s.total = s.stg_off + THREADS * STG_STRIDE * 4;
+    s.pi_off = s.stg_off + THREADS * STG_STRIDE * 4;
+    s.total = s.pi_off + (pim ? THREADS * PI_STRIDE * 4 : 0);
     return s;
   }
   // a variant serves N when a slice fits the slots and only a slice's last word is partial
-  __host__ static bool serves(int N) {
+  __host__ __device__ static bool serves(int N) {
     const int Jr = (N + S - 1) / S;
     return Jr >= TPW && Jr <= J && (NWORD == 1 || Jr - 1 >= 32 * (NWORD - 1));
   }
@@ -195,15 +199,18 @@ __host__ __device__ __forceinline__ void slice_of(int sigma, int S, int N, int& 
   start = sigma * Jr - (sigma > S - mshort ? sigma - (S - mshort) : 0);
 }
 
-template <int DIR, int TPW, int W, int KQ>
-__global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) {
+// PIM = 1: prior matrix.  Each lane keeps its slots' prior values pi_j (zero on padding and on
+// the diagonal) in shared memory; the forward adds rho * pi_j per cell and the backward sums
+// t_j pi_j, so no junk correction is needed.
+template <int DIR, int TPW, int W, int KQ, int PIM>
+__global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kernel(const PropParams p) {
   using C = PropCfg<TPW, W, KQ>;
   constexpr int SPW = C::SPW, S = C::S, NWORD = C::NWORD, THREADS = C::THREADS;
   constexpr int step_dir = DIR == 0 ? 1 : -1;
   extern __shared__ __align__(128) unsigned char smem[];
   const int N = p.N;
   const int rw2 = p.rw2;
-  const SmemLayout lay = C::layout(rw2);
+  const SmemLayout lay = C::layout(rw2, PIM);
   float* part = reinterpret_cast<float*>(smem + C::PART_OFF);
   float* lgr = reinterpret_cast<float*>(smem + C::LOGR_OFF);
   double* lgs = reinterpret_cast<double*>(smem + C::LOG_OFF);
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
   const int wb = b0 >> 5;
   const uint32_t wsh = (uint32_t)(b0 & 31);
   const int abit = o + tl;                      // bit of the target itself
-  const float n_junk = (float)(S * C::J - (N - 1));
+  const float n_junk = PIM ? 0.0f : (float)(S * C::J - (N - 1));
   const uint32_t dclear = (warp == 0 && sl == 0) ? ~(1u << tl) : 0xffffffffu;  // diagonal = slot tl of slice 0
   const int vl = len - 32 * (NWORD - 1);        // valid slots of the last word
   const uint32_t vmask_last = vl >= 32 ? 0xffffffffu : (vl <= 0 ? 0u : ((1u << vl) - 1u));
@@ -315,6 +322,22 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
       __syncthreads();
     }
   }
+  // prior values of this lane's slots (matrix prior): slot s <-> donor (start + s + o) mod N
+  const float* pis = reinterpret_cast<const float*>(smem + lay.pi_off) + tid * C::PI_STRIDE;
+  if (PIM) {
+    float* my = reinterpret_cast<float*>(smem + lay.pi_off) + tid * C::PI_STRIDE;
+    int tgt = o + tl;
+    tgt = tgt >= N ? tgt - N : tgt;
+    const float* prow = p.Pi + (size_t)tgt * N;
+    for (int s2 = 0; s2 < C::J; ++s2) {
+      int d = start + s2 + o;
+      d = d >= N ? d - N : d;
+      d = d >= N ? d - N : d;
+      my[s2] = (s2 < len && d != tgt) ? prow[d] : 0.0f;
+    }
+    __syncthreads();
+  }
+
   // store the tile (mode 0: x; 1: c x + r; 2: multiply the destination by c x + r)
   auto store_tile = [&](float* gbase, int mode, float c, float r) {
     const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
@@ -419,7 +442,7 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
     bool add_log_prev = false;
     if (step == 0 && p.init) {
       c = 0.0f;
-      r = DIR == 0 ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
+      r = (DIR == 0 && !PIM) ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
     } else if (step == 0 && DIR == 1) {
       c = 1.0f;  // backward resume: x = theta^l beta^l from the stored beta
       r = 0.0f;
@@ -478,12 +501,32 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
         if ((kn & 7) == 0) prep_word(kn >> 3);
         th[k % kLA] = load_th(kn);
       }
-      const f2 u01 = __ffma2_rn(C2, x[k][0], R2);
-      const f2 u23 = __ffma2_rn(C2, x[k][1], R2);
-      x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
-      x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
-      acc0 = __fadd2_rn(acc0, x[k][0]);
-      acc1 = __fadd2_rn(acc1, x[k][1]);
+      if (PIM) {
+        const float4 pv = *reinterpret_cast<const float4*>(pis + 4 * k);
+        const f2 p01 = make_float2(pv.x, pv.y), p23 = make_float2(pv.z, pv.w);
+        if (DIR == 0) {  // u = c x + rho pi_j
+          const f2 u01 = __ffma2_rn(C2, x[k][0], __fmul2_rn(R2, p01));
+          const f2 u23 = __ffma2_rn(C2, x[k][1], __fmul2_rn(R2, p23));
+          x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
+          x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
+          acc0 = __fadd2_rn(acc0, x[k][0]);
+          acc1 = __fadd2_rn(acc1, x[k][1]);
+        } else {         // S = sum_j t_j pi_j
+          const f2 u01 = __ffma2_rn(C2, x[k][0], R2);
+          const f2 u23 = __ffma2_rn(C2, x[k][1], R2);
+          x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
+          x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
+          acc0 = __ffma2_rn(x[k][0], p01, acc0);
+          acc1 = __ffma2_rn(x[k][1], p23, acc1);
+        }
+      } else {
+        const f2 u01 = __ffma2_rn(C2, x[k][0], R2);
+        const f2 u23 = __ffma2_rn(C2, x[k][1], R2);
+        x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
+        x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
+        acc0 = __fadd2_rn(acc0, x[k][0]);
+        acc1 = __fadd2_rn(acc1, x[k][1]);
+      }
     }
     xs = cur_thx * fmaf(c, xs, r);  // junk cells: theta = mu in every lane
 
@@ -504,7 +547,7 @@ __global__ void __launch_bounds__(W * 32, 2) ls_prop_kernel(const PropParams p) 
 
     const float tot = reduce((acc0.x + acc0.y) + (acc1.x + acc1.y), part + (step & 1) * TPW * W);
     float sig = tot - n_junk * xs;
-    if (DIR == 1) sig *= p.pi_u;
+    if (DIR == 1 && !PIM) sig *= p.pi_u;
     if (tid < TPW) lgr[tid * 32 + (step & 31)] = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
     if ((step & 31) == 31 || step == p.n_steps - 1) flush_logs((step & 31) + 1);
     sig_prev = sig;

@@ -8,16 +8,16 @@
 
 namespace {
 
-template <int TPW, int W, int KQ>
+template <int TPW, int W, int KQ, int PIM>
 cudaError_t launch_prop(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
-  if (dir == 0) lsk::ls_prop_kernel<0, TPW, W, KQ><<<grid, W * 32, smem, s>>>(p);
-  else lsk::ls_prop_kernel<1, TPW, W, KQ><<<grid, W * 32, smem, s>>>(p);
+  if (dir == 0) lsk::ls_prop_kernel<0, TPW, W, KQ, PIM><<<grid, W * 32, smem, s>>>(p);
+  else lsk::ls_prop_kernel<1, TPW, W, KQ, PIM><<<grid, W * 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int TPW, int W, int KQ>
+template <int TPW, int W, int KQ, int PIM>
 int smem_prop(int rw2) {
-  return lsk::PropCfg<TPW, W, KQ>::layout(rw2).total;
+  return lsk::PropCfg<TPW, W, KQ>::layout(rw2, PIM).total;
 }
 
 template <int TPW, int W, int KQ>
@@ -27,10 +27,12 @@ bool serves_prop(int N) {
 
 }  // namespace
 
-#define LS_REG(T, Wp, K)                                                                                  \
-  out.push_back(PropKernelInfo{T, Wp, K,                                                                  \
-                               {(const void*)lsk::ls_prop_kernel<0, T, Wp, K>, (const void*)lsk::ls_prop_kernel<1, T, Wp, K>}, \
-                               launch_prop<T, Wp, K>, smem_prop<T, Wp, K>, serves_prop<T, Wp, K>})
+#define LS_REGP(T, Wp, K, P)                                                                        \
+  out.push_back(PropKernelInfo{T, Wp, K, P,                                                         \
+                               {(const void*)lsk::ls_prop_kernel<0, T, Wp, K, P>,                   \
+                                (const void*)lsk::ls_prop_kernel<1, T, Wp, K, P>},                  \
+                               launch_prop<T, Wp, K, P>, smem_prop<T, Wp, K, P>, serves_prop<T, Wp, K>})
+#define LS_REG(T, Wp, K) LS_REGP(T, Wp, K, 0)
 
 #if LS_INST_GROUP == 0
 void ls_register_group0(std::vector<PropKernelInfo>& out) {
@@ -71,5 +73,20 @@ void ls_register_group5(std::vector<PropKernelInfo>& out) {
   LS_REG(1, 4, 16);
   LS_REG(1, 4, 8);
   LS_REG(1, 4, 1);
+}
+#elif LS_INST_GROUP == 6
+void ls_register_group6(std::vector<PropKernelInfo>& out) {
+  // prior-matrix variants: one target per CTA covers every N up to 20480
+  LS_REGP(1, 4, 1, 1);
+  LS_REGP(1, 4, 8, 1);
+  LS_REGP(1, 4, 16, 1);
+  LS_REGP(1, 4, 24, 1);
+}
+#elif LS_INST_GROUP == 7
+void ls_register_group7(std::vector<PropKernelInfo>& out) {
+  LS_REGP(1, 4, 32, 1);
+  LS_REGP(1, 4, 40, 1);
+  LS_REGP(1, 8, 20, 1);
+  LS_REGP(8, 4, 16, 1);
 }
 #endif

@@ -78,6 +78,17 @@ def gamma_prior(rng: np.random.Generator, N: int, rows=None) -> np.ndarray:
     return out
 
 
+def gamma_prior_f32(seed: int, N: int, chunk: int = 1024) -> np.ndarray:
+    """float32 [N, N] prior matrix of the Gamma(2, 1) workloads, drawn and normalised in float64
+    chunks of recipient rows (bounded host memory at N = 20000), then rounded to float32."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((N, N), dtype=np.float32)
+    for r0 in range(0, N, chunk):
+        rows = np.arange(r0, min(N, r0 + chunk))
+        out[rows] = gamma_prior(rng, N, rows).astype(np.float32)
+    return out
+
+
 def make_workload(name: str, N: int | None = None, L: int | None = None, seed: int | None = None) -> dict:
     """Draw the inputs of a workload (optionally shrunk to N x L for tests).
 

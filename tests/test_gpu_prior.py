@@ -1,0 +1,182 @@
+"""Prior-matrix propagation (Sec. 2.1 copying prior Pi, recipient-major rows) vs the FP64 oracle.
+
+The matrix-prior kernels keep each lane's prior values in shared memory: the forward adds
+rho * Pi_ij per cell and the backward normaliser is sum_j Pi_ij theta_j beta_j.  Both sides get
+the same float32 prior (the oracle reads it widened to float64), drawn from Gamma(2, 1) and
+row-normalised as in the dense-at-scale workload.  Tolerances are those of the uniform-prior tests.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_11403_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+D_TOL = 1e-5
+TAB_RTOL = 2e-4
+
+
+def log_close(got, ref, L, n=1):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    tol = 1e-6 * np.abs(ref) + 2e-7 * L * math.sqrt(n)
+    return bool(np.all(np.abs(got - ref) <= tol)), float(np.max(np.abs(got - ref)))
+
+
+def d_err(dg, dr):
+    dg = np.asarray(dg, dtype=np.float64)
+    return float(np.max(np.abs(dg - dr)) / max(1.0, float(np.max(np.abs(dr)))))
+
+
+def rel_close(got, ref, rtol, floor=1e-30):
+    got = np.asarray(got, dtype=np.float64)
+    m = np.abs(ref) > floor
+    e = float(np.max(np.abs(got[m] - ref[m]) / np.abs(ref[m]))) if m.any() else 0.0
+    return e <= rtol, e
+
+
+@pytest.fixture(scope="module")
+def ls():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2212_11403_gb300 import ls as _ls
+    return _ls
+
+
+def run_all_prior(ls, h, rho, mu, Pi32, loci, targets=None):
+    """ls_run_all with a prior matrix; returns (rc, pac, d or d among `targets`, status)."""
+    import torch
+    L, N = h.shape
+    ctx = ls.ls_create(h)
+    try:
+        ls.ls_set_params(ctx, rho, mu, torch.from_numpy(Pi32).cuda())
+        d = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+        st = torch.zeros(N, dtype=torch.int32, device="cuda")
+        rc, pac = ls.ls_run_all(ctx, loci, d, status_out=st)
+        if targets is not None:
+            ti = torch.from_numpy(np.asarray(targets, dtype=np.int64)).cuda()
+            d = d[:, ti][:, :, ti]
+        torch.cuda.synchronize()
+        return rc, pac, d.cpu().numpy(), st.cpu().numpy()
+    finally:
+        ls.ls_destroy(ctx)
+
+
+def test_prior_matrix_n200_l1000_full_parity(ls):
+    w = synth.make_workload("ls_n200_l1000")
+    Pi = synth.gamma_prior_f32(w["seed"] + 7, w["N"])
+    loci = w["loci"]
+    rc, pac, d, st = run_all_prior(ls, w["h"], w["rho"], w["mu"], Pi, loci)
+    assert rc == 0 and not st.any()
+    ref = oracle.run(w["h"], w["rho"], w["mu"], loci, Pi=Pi, want=("post", "llf"))
+    for k in range(len(loci)):
+        dref = oracle.distance_block(ref["post"][:, k, :], np.arange(w["N"]))
+        assert d_err(d[k], dref) <= D_TOL, (loci[k], d_err(d[k], dref))
+    assert log_close(pac, ref["llf"].sum(), w["L"], w["N"])[0]
+
+
+# every matrix-prior variant's range of N, with ragged slices; large N sampled by target
+@pytest.mark.parametrize("N", [2, 3, 7, 33, 130, 517, 4096, 4097, 8193, 12289, 16385, 20000])
+def test_prior_matrix_ragged_sizes(ls, N):
+    L = 40
+    w = synth.make_workload("ls_n5000_l20000", N=N, L=L, seed=500 + N)
+    Pi = synth.gamma_prior_f32(w["seed"] + 7, N)
+    loci = np.array([0, 17, L - 1], dtype=np.int32)
+    targets = None if N <= 600 else np.sort(np.random.default_rng(N).choice(N, size=24, replace=False))
+    rc, pac, d, st = run_all_prior(ls, w["h"], w["rho"], w["mu"], Pi, loci, targets)
+    assert rc == 0
+    ts = np.arange(N) if targets is None else targets
+    ref = oracle.run(w["h"], w["rho"], w["mu"], loci, targets=ts, Pi=Pi, want=("post", "llf"))
+    for k in range(len(loci)):
+        dref = oracle.distance_block(ref["post"][:, k, :], ts)
+        assert d_err(d[k], dref) <= D_TOL, (N, k, d_err(d[k], dref))
+        assert np.all(np.diag(d[k]) == 0.0)
+    if targets is None:
+        assert log_close(pac, ref["llf"].sum(), L, N)[0]
+
+
+def test_uniform_matrix_matches_uniform_prior(ls):
+    """Pi_ij = 1/(N-1) given as a matrix reproduces the scalar uniform prior (Sec. 3.3 default)."""
+    import torch
+    w = synth.make_workload("ls_n5000_l20000", N=700, L=120, seed=41)
+    N = w["N"]
+    Pi = np.full((N, N), 1.0 / (N - 1), dtype=np.float32)
+    np.fill_diagonal(Pi, 0.0)
+    loci = np.array([3, 60, 119], dtype=np.int32)
+    rc, pac, d, _ = run_all_prior(ls, w["h"], w["rho"], w["mu"], Pi, loci)
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        du = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+        rcu, pacu = ls.ls_run_all(ctx, loci, du)
+        torch.cuda.synchronize()
+        du = du.cpu().numpy()
+    finally:
+        ls.ls_destroy(ctx)
+    assert rc == rcu == 0
+    assert d_err(d, du.astype(np.float64)) <= D_TOL
+    assert abs(pac - pacu) <= 1e-6 * abs(pacu) + 2e-7 * 120 * math.sqrt(N)
+
+
+def test_prior_matrix_tables_and_resume(ls):
+    """forward/backward tables with stores, resumed in pieces, against the oracle."""
+    import torch
+    w = synth.make_workload("ls_n200_l1000", N=150, L=300, seed=6)
+    N, L = w["N"], w["L"]
+    Pi = synth.gamma_prior_f32(11, N)
+    t0, t1 = 20, 70
+    T = t1 - t0
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"], torch.from_numpy(Pi).cuda())
+        fw = ls.ls_table_create(ctx, ls.LS_FWD, t0, t1)
+        bw = ls.ls_table_create(ctx, ls.LS_BWD, t0, t1)
+        A = torch.empty((2, T, N), dtype=torch.float32, device="cuda")
+        ls.ls_forward(ctx, fw, 40, [0], A[:1])
+        ls.ls_forward(ctx, fw, 150, [150], A[1:])
+        B = torch.empty((2, T, N), dtype=torch.float32, device="cuda")
+        ls.ls_backward(ctx, bw, 220, [299], B[:1])
+        ls.ls_backward(ctx, bw, 150, [150], B[1:])
+        P = torch.empty((T, N), dtype=torch.float32, device="cuda")
+        ls.ls_posterior(ctx, fw, bw, P)
+        lf = torch.empty(T, dtype=torch.float64, device="cuda")
+        ls.ls_table_read(fw, logscale=lf)
+        torch.cuda.synchronize()
+        ref = oracle.run(w["h"], w["rho"], w["mu"], [0, 150, 299], targets=np.arange(t0, t1), Pi=Pi,
+                         want=("alpha", "beta", "post", "logF"))
+        A, B, P = A.cpu().numpy(), B.cpu().numpy(), P.cpu().numpy()
+        assert rel_close(A[0], ref["alpha"][:, 0, :], TAB_RTOL)[0]
+        assert rel_close(A[1], ref["alpha"][:, 1, :], TAB_RTOL)[0]
+        assert rel_close(B[0], ref["beta"][:, 2, :], TAB_RTOL)[0]
+        assert rel_close(B[1], ref["beta"][:, 1, :], TAB_RTOL)[0]
+        ok, e = rel_close(P, ref["post"][:, 1, :], TAB_RTOL, floor=1e-12)
+        assert ok, e
+        np.testing.assert_allclose(P.sum(axis=1), 1.0, rtol=1e-5)
+        assert log_close(lf.cpu().numpy(), ref["logF"][:, 1], 151)[0]
+        ls.ls_table_destroy(fw)
+        ls.ls_table_destroy(bw)
+    finally:
+        ls.ls_destroy(ctx)
+
+
+def test_prior_matrix_n20000_l50000_sampled_targets(ls):
+    """Dense LS at scale with the Gamma(2, 1) prior matrix at its full size (N = 20000,
+    L = 50000, rho from exponential map gaps): d among 16 seeded-random targets against the
+    oracle."""
+    w = synth.make_workload("ls_n20000_l50000")
+    N, L, loci = w["N"], w["L"], w["loci"]
+    rho_gpu = ls.ls_calc_rho(w["gaps"], w["Ne"], 1.0)
+    rho_ref = oracle.calc_rho(w["gaps"], w["Ne"], 1.0)
+    np.testing.assert_allclose(rho_gpu, rho_ref, rtol=1e-14, atol=0)
+    Pi = synth.gamma_prior_f32(w["pi_seed"], N)
+    targets = np.sort(np.random.default_rng(2025).choice(N, size=16, replace=False))
+    rc, pac, d, st = run_all_prior(ls, w["h"], rho_gpu, w["mu"], Pi, loci, targets)
+    assert rc == 0 and math.isfinite(pac)
+    ref = oracle.run(w["h"], rho_ref, w["mu"], loci, targets=targets, Pi=Pi, want=("post",))
+    del Pi
+    for k in range(len(loci)):
+        dref = oracle.distance_block(ref["post"][:, k, :], targets)
+        assert d_err(d[k], dref) <= D_TOL, (loci[k], d_err(d[k], dref))
