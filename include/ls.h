@@ -56,6 +56,7 @@ extern "C" {
 typedef void* ls_stream_t; /* a cudaStream_t */
 typedef struct ls_ctx ls_ctx;
 typedef struct ls_table ls_table;
+typedef struct ls_ckpt ls_ckpt;
 
 /* Library version and build description (arch, kernel variants).  Static string. */
 const char* ls_version(void);
@@ -146,6 +147,44 @@ int ls_forward(ls_ctx* ctx, ls_table* fwd, int32_t to_locus, const int32_t* stor
  * ls_forward. */
 int ls_backward(ls_ctx* ctx, ls_table* bck, int32_t to_locus, const int32_t* store_loci, int32_t n_store,
                 float* beta_out, uint32_t* status_out, ls_stream_t stream);
+
+/* ---- forward checkpoints and replay ---------------------------------------------------------
+ * The paper keeps one locus per table and resumes by propagating again (Sec. 3.5); to revisit
+ * earlier loci without a full new pass, ls_checkpoints snapshots alpha at the K = ceil(log2(b-a+1))
+ * recursive-bisection loci of [a, b]: c_0 = a and c_k = b - floor((b-a) / 2^k) for k = 1..K-1 (the
+ * halving points, densest where a backward sweep starts).  A snapshot is the table's state
+ * [T][N] and log F [T] at that locus.  LS_CKPT_F32 keeps alpha exactly; LS_CKPT_F16 stores, per
+ * target, s = max_j alpha_j (float) and alpha_j / s rounded to nearest binary16: entries at or
+ * above 2^-14 s keep a relative error of at most 2^-11, smaller ones an absolute error of at most
+ * 2^-25 s (those below 2^-25 s become 0). */
+#define LS_CKPT_F32 0
+#define LS_CKPT_F16 1
+
+/* Propagate fwd (an LS_FWD table at a locus <= a, or uninitialised) to locus b, taking the K
+ * snapshots on the way; 0 <= a <= b < L.  *out receives a new checkpoint set owning
+ * K * T * N * (4 or 2) bytes of device memory (+ K * T * 12 bytes).  status_out as ls_forward.
+ * Errors: LS_ERR_DIRECTION (fwd beyond a), LS_ERR_PARAM_MISMATCH, LS_ERR_OOM. */
+int ls_checkpoints(ls_ctx* ctx, ls_table* fwd, int32_t a, int32_t b, int32_t dtype, ls_ckpt** out,
+                   uint32_t* status_out, ls_stream_t stream);
+
+/* Number of snapshots, their loci (host int32 [K], may be NULL), dtype, target range and the
+ * device bytes held. */
+int ls_ckpt_info(const ls_ckpt* ck, int32_t* n, int32_t* loci, int32_t* dtype, int32_t* t_from, int32_t* t_to,
+                 size_t* device_bytes);
+
+/* Snapshot k decoded to FP32: alpha_out device float [T][N] and logF_out device double [T]
+ * (either may be NULL).  Enqueued on stream. */
+int ls_ckpt_read(const ls_ckpt* ck, int32_t k, float* alpha_out, double* logF_out, ls_stream_t stream);
+
+/* Replay: set fwd (same context and target range as the checkpoints) to the snapshot with the
+ * largest c_k <= locus, decoded to FP32, and propagate it forward to locus (c_0 <= locus < L),
+ * whatever fwd held before.  Errors: LS_ERR_RANGE, LS_ERR_PARAM_MISMATCH (the parameters
+ * changed since the checkpoints were taken). */
+int ls_ckpt_replay(ls_ctx* ctx, const ls_ckpt* ck, ls_table* fwd, int32_t locus, uint32_t* status_out,
+                   ls_stream_t stream);
+
+/* Free a checkpoint set. */
+int ls_ckpt_destroy(ls_ckpt* ck);
 
 /* PostProbs (Eq. postprob): p_out device float [T][N], p_out[r*N+j] = posterior that target
  * t_from+r copies donor j; p = epsilon (DBL_EPSILON) for every donor if the normaliser is 0;

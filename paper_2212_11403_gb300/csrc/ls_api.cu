@@ -632,6 +632,131 @@ int ls_backward(ls_ctx* ctx, ls_table* bck, int32_t to_locus, const int32_t* sto
   return propagate(ctx, bck, 1, to_locus, store_loci, n_store, beta_out, status_out, stream);
 }
 
+// ---- forward checkpoints (recursive-bisection loci) and replay --------------------------------
+static void ckpt_free(ls_ckpt* ck) {
+  cudaFree(ck->data);
+  cudaFree(ck->scale);
+  cudaFree(ck->logs);
+  delete ck;
+}
+
+int ls_checkpoints(ls_ctx* ctx, ls_table* fwd, int32_t a, int32_t b, int32_t dtype, ls_ckpt** out,
+                   uint32_t* status_out, ls_stream_t stream) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!out) return fail(LS_ERR_ARG, "null output");
+  if (!fwd || fwd->ctx != ctx || fwd->kind != LS_FWD) return fail(LS_ERR_ARG, "need a forward table of this context");
+  if (dtype != LS_CKPT_F32 && dtype != LS_CKPT_F16) return fail(LS_ERR_ARG, "dtype must be LS_CKPT_F32 or LS_CKPT_F16");
+  if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
+  if (!(0 <= a && a <= b && b < ctx->L)) return fail(LS_ERR_ARG, "bad locus range [%d, %d]", a, b);
+  if (fwd->locus > a) return fail(LS_ERR_DIRECTION, "forward table at locus %d is beyond a = %d", fwd->locus, a);
+  if (fwd->locus >= 0 && fwd->hash != ctx->hash)
+    return fail(LS_ERR_PARAM_MISMATCH, "table was propagated under another parameter set");
+  // K = ceil(log2(b - a + 1)) snapshots (one when a == b): c_0 = a, c_k = b - floor((b - a) / 2^k)
+  int K = 1;
+  while ((1ll << K) < (long long)(b - a + 1)) ++K;
+  ls_ckpt* ck = new ls_ckpt;
+  ck->ctx = ctx;
+  ck->dtype = dtype;
+  ck->t_from = fwd->t_from;
+  ck->t_to = fwd->t_to;
+  ck->loci.push_back(a);
+  for (int k = 1; k < K; ++k) ck->loci.push_back(b - (int)((long long)(b - a) >> k));
+  const size_t T = (size_t)(fwd->t_to - fwd->t_from), N = (size_t)ctx->N;
+  const size_t esz = dtype == LS_CKPT_F16 ? 2 : 4;
+  if ((rc = dev_alloc(nullptr, &ck->data, (size_t)K * T * N * esz)) ||
+      (rc = dev_alloc(nullptr, (void**)&ck->logs, sizeof(double) * K * T)) ||
+      (dtype == LS_CKPT_F16 && (rc = dev_alloc(nullptr, (void**)&ck->scale, sizeof(float) * K * T)))) {
+    ckpt_free(ck);
+    return rc;
+  }
+  ck->bytes = (size_t)K * T * (N * esz + 8 + (dtype == LS_CKPT_F16 ? 4 : 0));
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int k = 0; k < K; ++k) {
+    if ((rc = propagate(ctx, fwd, 0, ck->loci[k], nullptr, 0, nullptr, status_out, stream))) {
+      ckpt_free(ck);
+      return rc;
+    }
+    if (dtype == LS_CKPT_F32) {
+      CUDA_TRY(cudaMemcpyAsync(static_cast<float*>(ck->data) + k * T * N, fwd->state, sizeof(float) * T * N,
+                               cudaMemcpyDeviceToDevice, s));
+    } else {
+      lsk::ckpt_encode_f16_kernel<<<(unsigned)T, 256, 0, s>>>(fwd->state, (int)N, static_cast<__half*>(ck->data) + k * T * N,
+                                                              ck->scale + k * T);
+      CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(cudaMemcpyAsync(ck->logs + k * T, fwd->logs, sizeof(double) * T, cudaMemcpyDeviceToDevice, s));
+  }
+  if ((rc = propagate(ctx, fwd, 0, b, nullptr, 0, nullptr, status_out, stream))) {
+    ckpt_free(ck);
+    return rc;
+  }
+  ck->hash = ctx->hash;
+  *out = ck;
+  return LS_OK;
+}
+
+int ls_ckpt_info(const ls_ckpt* ck, int32_t* n, int32_t* loci, int32_t* dtype, int32_t* t_from, int32_t* t_to,
+                 size_t* device_bytes) {
+  if (!ck) return fail(LS_ERR_ARG, "null checkpoint set");
+  if (n) *n = (int32_t)ck->loci.size();
+  if (loci)
+    for (size_t k = 0; k < ck->loci.size(); ++k) loci[k] = ck->loci[k];
+  if (dtype) *dtype = ck->dtype;
+  if (t_from) *t_from = ck->t_from;
+  if (t_to) *t_to = ck->t_to;
+  if (device_bytes) *device_bytes = ck->bytes;
+  return LS_OK;
+}
+
+static int ckpt_decode(const ls_ckpt* ck, int k, float* alpha, double* logs, cudaStream_t s) {
+  const size_t T = (size_t)(ck->t_to - ck->t_from), N = (size_t)ck->ctx->N;
+  if (alpha) {
+    if (ck->dtype == LS_CKPT_F32) {
+      CUDA_TRY(cudaMemcpyAsync(alpha, static_cast<const float*>(ck->data) + k * T * N, sizeof(float) * T * N,
+                               cudaMemcpyDeviceToDevice, s));
+    } else {
+      lsk::ckpt_decode_f16_kernel<<<(unsigned)T, 256, 0, s>>>(static_cast<const __half*>(ck->data) + k * T * N,
+                                                              ck->scale + k * T, (int)N, alpha);
+      CUDA_TRY(cudaGetLastError());
+    }
+  }
+  if (logs) CUDA_TRY(cudaMemcpyAsync(logs, ck->logs + k * T, sizeof(double) * T, cudaMemcpyDeviceToDevice, s));
+  return LS_OK;
+}
+
+int ls_ckpt_read(const ls_ckpt* ck, int32_t k, float* alpha_out, double* logF_out, ls_stream_t stream) {
+  if (!ck) return fail(LS_ERR_ARG, "null checkpoint set");
+  if (k < 0 || k >= (int)ck->loci.size()) return fail(LS_ERR_ARG, "snapshot %d out of range [0, %zu)", k, ck->loci.size());
+  cudaSetDevice(ck->ctx->device);
+  return ckpt_decode(ck, k, alpha_out, logF_out, (cudaStream_t)stream);
+}
+
+int ls_ckpt_replay(ls_ctx* ctx, const ls_ckpt* ck, ls_table* fwd, int32_t locus, uint32_t* status_out,
+                   ls_stream_t stream) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!ck || ck->ctx != ctx) return fail(LS_ERR_ARG, "checkpoints do not belong to this context");
+  if (!fwd || fwd->ctx != ctx || fwd->kind != LS_FWD) return fail(LS_ERR_ARG, "need a forward table of this context");
+  if (fwd->t_from != ck->t_from || fwd->t_to != ck->t_to) return fail(LS_ERR_RANGE, "table and checkpoints cover different targets");
+  if (ck->hash != ctx->hash) return fail(LS_ERR_PARAM_MISMATCH, "checkpoints were taken under another parameter set");
+  if (locus < ck->loci[0] || locus >= ctx->L)
+    return fail(LS_ERR_ARG, "locus %d outside [%d, %d)", locus, ck->loci[0], ctx->L);
+  int k = (int)ck->loci.size() - 1;
+  while (ck->loci[k] > locus) --k;
+  if ((rc = ckpt_decode(ck, k, fwd->state, fwd->logs, (cudaStream_t)stream))) return rc;
+  fwd->locus = ck->loci[k];
+  fwd->hash = ck->hash;
+  return propagate(ctx, fwd, 0, locus, nullptr, 0, nullptr, status_out, stream);
+}
+
+int ls_ckpt_destroy(ls_ckpt* ck) {
+  if (!ck) return fail(LS_ERR_ARG, "null checkpoint set");
+  cudaSetDevice(ck->ctx->device);
+  ckpt_free(ck);
+  return LS_OK;
+}
+
 static int check_pair(ls_ctx* ctx, const ls_table* fwd, const ls_table* bck) {
   int rc = check_ctx(ctx);
   if (rc) return rc;

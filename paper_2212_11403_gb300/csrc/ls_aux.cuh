@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "ls_prop.cuh"
@@ -129,6 +130,54 @@ __global__ void symmetrize_kernel(float* __restrict__ d, int N) {
       if (rb < N && cb < N) m[(size_t)rb * N + cb] = B[k][tx] + A[tx][k];
     }
   }
+}
+
+// Binary16 checkpoint of one forward state row per block: scale = max_j alpha_j (NaN when the row
+// holds a non-finite value), q_j = alpha_j / scale rounded to nearest binary16 (0 for a zero row).
+__global__ void ckpt_encode_f16_kernel(const float* __restrict__ alpha, int N, __half* __restrict__ q,
+                                       float* __restrict__ scale) {
+  __shared__ float wmax[32];
+  __shared__ int wbad[32];
+  const size_t row = blockIdx.x;
+  const float* x = alpha + row * (size_t)N;
+  float m = 0.0f;
+  int bad = 0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const float v = x[j];
+    if (!(v <= 3.40282347e+38f)) bad = 1;
+    m = fmaxf(m, v);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    wmax[warp] = m;
+    wbad[warp] = bad;
+  }
+  __syncthreads();
+  m = 0.0f;
+  bad = 0;
+  for (int w = 0; w < nw; ++w) {
+    m = fmaxf(m, wmax[w]);
+    bad |= wbad[w];
+  }
+  const float sc = bad ? __int_as_float(0x7fc00000) : m;
+  if (threadIdx.x == 0) scale[row] = sc;
+  __half* qr = q + row * (size_t)N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) qr[j] = __float2half_rn(sc > 0.0f ? x[j] / sc : 0.0f);
+}
+
+// Inverse of ckpt_encode_f16_kernel: alpha_j = q_j * scale, one row per block.
+__global__ void ckpt_decode_f16_kernel(const __half* __restrict__ q, const float* __restrict__ scale, int N,
+                                       float* __restrict__ alpha) {
+  const size_t row = blockIdx.x;
+  const float sc = scale[row];
+  const __half* qr = q + row * (size_t)N;
+  float* x = alpha + row * (size_t)N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) x[j] = __half2float(qr[j]) * sc;
 }
 
 }  // namespace lsk

@@ -54,6 +54,18 @@ struct ls_ctx {
   int launches[4] = {0, 0, 0, 0};
 };
 
+struct ls_ckpt {
+  ls_ctx* ctx = nullptr;
+  int dtype = 0;
+  int t_from = 0, t_to = 0;
+  std::vector<int> loci;     // c_0 < c_1 < ... < c_{K-1}
+  uint64_t hash = 0;
+  void* data = nullptr;      // [K][T][N] float or binary16
+  float* scale = nullptr;    // [K][T] (binary16 only)
+  double* logs = nullptr;    // [K][T]
+  size_t bytes = 0;
+};
+
 struct ls_table {
   ls_ctx* ctx = nullptr;
   int kind = 0;

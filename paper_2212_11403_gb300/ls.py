@@ -34,11 +34,14 @@ LS_STATUS_TIMEOUT = 4
 LS_FWD = 0
 LS_BWD = 1
 LS_NOALLOC_MAX_N = 65536
+LS_CKPT_F32 = 0
+LS_CKPT_F16 = 1
 
 EXPORTED = [
     "ls_version", "ls_last_error", "ls_create", "ls_create_packed", "ls_destroy", "ls_info", "ls_query",
     "ls_export_packed", "ls_calc_rho", "ls_set_params", "ls_table_create", "ls_table_destroy", "ls_table_copy",
     "ls_table_reset", "ls_table_info", "ls_table_read", "ls_forward", "ls_backward", "ls_posterior", "ls_distance",
+    "ls_checkpoints", "ls_ckpt_info", "ls_ckpt_read", "ls_ckpt_replay", "ls_ckpt_destroy",
     "ls_run_all", "ls_run_all_noalloc", "ls_set_profiling", "ls_profile_read",
 ]
 
@@ -74,6 +77,11 @@ def _load():
         "ls_table_read": ([P, P, P, P], I),
         "ls_forward": ([P, P, I, P, I, P, P, P], I),
         "ls_backward": ([P, P, I, P, I, P, P, P], I),
+        "ls_checkpoints": ([P, P, I, I, I, P, P, P], I),
+        "ls_ckpt_info": ([P, P, P, P, P, P, P], I),
+        "ls_ckpt_read": ([P, I, P, P, P], I),
+        "ls_ckpt_replay": ([P, P, P, I, P, P], I),
+        "ls_ckpt_destroy": ([P], I),
         "ls_posterior": ([P, P, P, P, P], I),
         "ls_distance": ([P, P, P, P, P], I),
         "ls_run_all": ([P, P, I, P, P, P, P], I),
@@ -232,6 +240,40 @@ def ls_forward(ctx, fwd, to_locus, store_loci=None, alpha_out=None, status_out=N
 
 def ls_backward(ctx, bck, to_locus, store_loci=None, beta_out=None, status_out=None, stream=None):
     return _prop(_lib.ls_backward, ctx, bck, to_locus, store_loci, beta_out, status_out, stream)
+
+
+def ls_checkpoints(ctx, fwd, a, b, dtype=LS_CKPT_F32, status_out=None, stream=None):
+    """snapshots of alpha at the recursive-bisection loci of [a, b]; returns the checkpoint handle."""
+    import torch
+    out = ctypes.c_void_p()
+    _check(_lib.ls_checkpoints(ctx, fwd, int(a), int(b), int(dtype), ctypes.byref(out),
+                               _dev(status_out, torch.int32, "status"), _stream(stream)))
+    return out
+
+
+def ls_ckpt_info(ck):
+    n, dt, a, b, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    _check(_lib.ls_ckpt_info(ck, ctypes.byref(n), None, None, None, None, None))
+    loci = np.zeros(n.value, dtype=np.int32)
+    _check(_lib.ls_ckpt_info(ck, ctypes.byref(n), loci.ctypes.data_as(ctypes.c_void_p), ctypes.byref(dt),
+                             ctypes.byref(a), ctypes.byref(b), ctypes.byref(nb)))
+    return dict(n=n.value, loci=loci, dtype=dt.value, t_from=a.value, t_to=b.value, device_bytes=nb.value)
+
+
+def ls_ckpt_read(ck, k, alpha_out=None, logF_out=None, stream=None):
+    import torch
+    return _check(_lib.ls_ckpt_read(ck, int(k), _dev(alpha_out, torch.float32, "alpha_out"),
+                                    _dev(logF_out, torch.float64, "logF_out"), _stream(stream)))
+
+
+def ls_ckpt_replay(ctx, ck, fwd, locus, status_out=None, stream=None):
+    import torch
+    return _check(_lib.ls_ckpt_replay(ctx, ck, fwd, int(locus), _dev(status_out, torch.int32, "status"),
+                                      _stream(stream)))
+
+
+def ls_ckpt_destroy(ck):
+    return _check(_lib.ls_ckpt_destroy(ck))
 
 
 def ls_posterior(ctx, fwd, bck, p_out, stream=None):
