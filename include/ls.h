@@ -206,6 +206,22 @@ int ls_distance(ls_ctx* ctx, const ls_table* fwd, const ls_table* bck, float* d_
 int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out, double* pac_out,
                uint32_t* status_out, ls_stream_t stream);
 
+/* ---- adjoint: gradient of the PAC log-likelihood --------------------------------------------
+ * The PAC log-likelihood of targets [t_from, t_to), sum_i log P(h_i | h_-i) (Sec. 1, Eq. F at the
+ * last locus), and its gradient with respect to log mu (one scalar scale of every mu_l) and to
+ * log rho on K groups of intervals: interval m (between loci m and m+1) belongs to group
+ * interval_of[m] (host int32 [L-1], nondecreasing, in [0, K)), and dlogrho[k] is the derivative
+ * with respect to a common log-scale of the rho_m of group k.  The paper defines no gradient;
+ * this one is the score by the Fisher identity (posterior expectation of the complete-data score
+ * of Eq. transition and App. A.3's emission), computed by two forward statistic passes and one
+ * backward pass in FP32 with FP64 sums.  Outputs are host doubles (any may be NULL); dlogrho has
+ * K entries, 0 for groups without intervals.  Device memory: 3 * (number of nonempty groups) *
+ * T * N floats + 2 * T * N floats, allocated for the call and freed before it returns.
+ * Synchronous.  Requires the uniform prior (LS_ERR_UNSUPPORTED otherwise), rho < 1 and mu < 1.
+ * Returns LS_WARN_* like ls_run_all. */
+int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interval_of, int32_t K,
+                double* pac_out, double* dlogmu_out, double* dlogrho_out, ls_stream_t stream);
+
 /* ---- fused pipeline without allocation --------------------------------------------------- */
 
 /* Largest N the allocation-free pipeline accepts: its scratch is a fixed area inside the library

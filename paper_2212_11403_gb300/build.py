@@ -25,7 +25,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
 # (source, extra defines, object name)
 UNITS = [
     ("ls_api.cu", [], "ls_api.o"),
-] + [("ls_prop_inst.cu", ["-DLS_INST_GROUP=%d" % g], "ls_prop_g%d.o" % g) for g in range(8)]
+] + [("ls_prop_inst.cu", ["-DLS_INST_GROUP=%d" % g], "ls_prop_g%d.o" % g) for g in range(10)]
 
 
 def nvcc() -> str:

@@ -22,6 +22,8 @@ void ls_register_group4(std::vector<PropKernelInfo>& out);
 void ls_register_group5(std::vector<PropKernelInfo>& out);
 void ls_register_group6(std::vector<PropKernelInfo>& out);
 void ls_register_group7(std::vector<PropKernelInfo>& out);
+void ls_register_group8(std::vector<PropKernelInfo>& out);
+void ls_register_group9(std::vector<PropKernelInfo>& out);
 
 namespace {
 
@@ -55,6 +57,8 @@ std::vector<PropKernelInfo>& registry() {
     ls_register_group5(v);
     ls_register_group6(v);
     ls_register_group7(v);
+    ls_register_group8(v);
+    ls_register_group9(v);
   });
   return v;
 }
@@ -96,7 +100,7 @@ std::vector<Cand> candidates(ls_ctx* c) {
   const int N = c->N;
   const int pim = c->Pi ? 1 : 0;
   for (const auto& k : registry()) {
-    if (k.pim != pim || !k.serves(N)) continue;
+    if (k.st != 0 || k.pim != pim || !k.serves(N)) continue;
     const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;
     bool ok = true;
@@ -469,6 +473,8 @@ int ls_set_params(ls_ctx* ctx, const double* rho, const double* mu, int32_t mu_l
   }
   ctx->pi_u = (float)pi_u;
   ctx->mu_vec = mu_len > 1 ? 1 : 0;
+  ctx->rho_h.assign(rho, rho + std::max(L - 1, 0));
+  ctx->mu_h.assign(mu, mu + mu_len);
   ctx->hash = h;
   ctx->have_params = true;
   if (hash_out) *hash_out = h;
@@ -898,6 +904,238 @@ int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out,
   return LS_OK;
 }
 
+// ---- adjoint: gradient of the PAC log-likelihood ------------------------------------------------
+// Fisher identity: the score is the posterior expectation of the complete-data score.  With the
+// recombination event B_m of interval m (probability rho_m, Eq. transition) and the mismatch
+// indicator H_l (emission mu, App. A.3), per target
+//   d log P / d log rho_m = (E[B_m] - rho_m) / (1 - rho_m),
+//   d log P / d log mu    = sum_l (E[H_l] - mu_l) / (1 - mu_l)        (donors j != i, sum_j p_j = 1).
+// E[sum_{m in I_k} B_m / (1 - rho_m)] for each group I_k of intervals comes from one forward
+// statistic pass (ST 1, restarted per group, alpha and w stored at the group's end locus) and one
+// backward pass (beta at those loci); E[sum_l H_l / (1 - mu_l)] from a second forward pass (ST 2)
+// read at the last locus, where beta = 1.
+}  // extern "C"
+
+namespace {
+struct StatPick {
+  const PropKernelInfo* k = nullptr;
+  int smem = 0;
+};
+
+int pick_stat(ls_ctx* c, StatPick* out) {
+  double bc = 1e300;
+  for (const auto& k : registry()) {
+    if (k.st != 1 || !k.serves(c->N)) continue;
+    const int smem = k.smem_bytes(c->rw2);
+    if (smem > 227 * 1024) continue;
+    bool ok = true;
+    for (int d = 0; d < 2 && ok; ++d)
+      if (cudaFuncSetAttribute(k.func[d], cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) ok = false;
+    int nb = 0;
+    if (ok && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.func[1], k.w * 32, smem) != cudaSuccess || nb < 1))
+      ok = false;
+    if (!ok) {
+      cudaGetLastError();
+      continue;
+    }
+    const double cc = cost_of(Cand{&k, smem, nb}, c->N, c->num_sms);
+    if (cc < bc) {
+      bc = cc;
+      out->k = &k;
+      out->smem = smem;
+    }
+  }
+  if (!out->k) return fail(LS_ERR_UNSUPPORTED, "no compiled statistic-pass variant serves N=%d", c->N);
+  return LS_OK;
+}
+
+struct DevBufs {
+  std::vector<void*> v;
+  ~DevBufs() {
+    for (void* p : v) cudaFree(p);
+  }
+  template <class T>
+  int get(T** p, size_t n) {
+    int rc = dev_alloc(nullptr, (void**)p, sizeof(T) * std::max<size_t>(n, 1));
+    if (!rc) v.push_back(*p);
+    return rc;
+  }
+};
+}  // namespace
+
+extern "C" {
+
+int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interval_of, int32_t K, double* pac_out,
+                double* dlogmu_out, double* dlogrho_out, ls_stream_t stream) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
+  if (ctx->Pi) return fail(LS_ERR_UNSUPPORTED, "the adjoint supports the uniform prior only");
+  const int N = ctx->N, L = ctx->L;
+  if (!(0 <= t_from && t_from < t_to && t_to <= N)) return fail(LS_ERR_ARG, "bad target range [%d, %d)", t_from, t_to);
+  if (K < 1 || (L > 1 && !interval_of)) return fail(LS_ERR_ARG, "need K >= 1 and interval_of[L-1]");
+  for (int m = 0; m + 1 < L; ++m) {
+    if (interval_of[m] < 0 || interval_of[m] >= K) return fail(LS_ERR_ARG, "interval_of[%d] = %d outside [0, %d)", m, interval_of[m], K);
+    if (m && interval_of[m] < interval_of[m - 1]) return fail(LS_ERR_ARG, "interval_of must be nondecreasing");
+    if (!(ctx->rho_h[m] < 1.0)) return fail(LS_ERR_ARG, "the gradient needs rho < 1 (rho[%d] = %g)", m, ctx->rho_h[m]);
+  }
+  for (double m : ctx->mu_h)
+    if (!(m < 1.0)) return fail(LS_ERR_ARG, "the gradient needs mu < 1");
+  StatPick sp;
+  if ((rc = pick_stat(ctx, &sp))) return rc;
+  const int T = t_to - t_from;
+  cudaStream_t s = (cudaStream_t)stream;
+  // groups with at least one interval; their end loci e_g (the locus after the group's last interval)
+  std::vector<int> gk, ge;
+  for (int m = 0; m + 1 < L; ++m) {
+    if (m + 1 == L - 1 || interval_of[m + 1] != interval_of[m]) {
+      gk.push_back(interval_of[m]);
+      ge.push_back(m + 1);
+    }
+  }
+  const int G = (int)gk.size();
+  if (G > 65535) return fail(LS_ERR_UNSUPPORTED, "at most 65535 nonempty intervals");
+  std::vector<float> gam(std::max(L - 1, 1), 1.0f), eta(L);
+  std::vector<uint8_t> rst(std::max(L - 1, 1), 0);
+  for (int m = 0; m + 1 < L; ++m) {
+    gam[m] = (float)(1.0 / (1.0 - ctx->rho_h[m]));
+    rst[m] = (m == 0 || interval_of[m] != interval_of[m - 1]) ? 1 : 0;
+  }
+  for (int l = 0; l < L; ++l) eta[l] = (float)(1.0 / (1.0 - ctx->mu_h[ctx->mu_h.size() > 1 ? l : 0]));
+  DevBufs db;
+  float *d_gam, *d_eta, *A, *Wst, *B, *xst, *wst;
+  uint8_t* d_rst;
+  double *logF, *EM, *Rg, *sums;
+  uint32_t* stat;
+  const size_t TN = (size_t)T * N;
+  if ((rc = db.get(&d_gam, gam.size())) || (rc = db.get(&d_eta, eta.size())) || (rc = db.get(&d_rst, rst.size())) ||
+      (rc = db.get(&A, (size_t)G * TN)) || (rc = db.get(&Wst, (size_t)G * TN)) || (rc = db.get(&B, (size_t)G * TN)) ||
+      (rc = db.get(&xst, TN)) || (rc = db.get(&wst, TN)) || (rc = db.get(&logF, T)) || (rc = db.get(&EM, T)) ||
+      (rc = db.get(&Rg, (size_t)std::max(G, 1) * T)) || (rc = db.get(&sums, (size_t)G + 2)) || (rc = db.get(&stat, T)))
+    return rc;
+  CUDA_TRY(cudaMemcpyAsync(d_gam, gam.data(), sizeof(float) * gam.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d_eta, eta.data(), sizeof(float) * eta.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d_rst, rst.data(), rst.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(uint32_t) * T, s));
+  const int grid = (T + sp.k->tpw - 1) / sp.k->tpw;
+  auto launch = [&](int which, lsk::PropParams& p) -> int {
+    p.t_begin = t_from;
+    p.t_count = T;
+    cudaError_t e = sp.k->launch(which, p, grid, sp.smem, s);
+    if (e != cudaSuccess) return fail(LS_ERR_CUDA, "statistic pass launch: %s", cudaGetErrorString(e));
+    return LS_OK;
+  };
+  // forward statistic pass 1 (recombinations per group), alpha and w stored at the group ends,
+  // in launches of at most kMaxStore stores that carry alpha and w between them
+  {
+    int k0 = 0, pos = -1;
+    do {
+      const int k1 = std::min(G, k0 + lsk::kMaxStore);
+      const int seg_end = k1 < G ? ge[k1 - 1] : L - 1;
+      lsk::PropParams p;
+      base_params(ctx, p, 0);
+      p.l_first = pos + 1;
+      p.n_steps = seg_end - pos;
+      p.init = pos < 0 ? 1 : 0;
+      p.load_state = pos < 0 ? 0 : 1;
+      p.save_state = 1;
+      p.tab_t0 = t_from;
+      p.state_rows = T;
+      p.state = xst;
+      p.wstate = wst;
+      p.logs = logF;
+      p.status = stat;
+      p.gam = d_gam;
+      p.reset = d_rst;
+      p.n_store = k1 - k0;
+      for (int k = k0; k < k1; ++k) {
+        p.store_loci[k - k0] = ge[k];
+        p.store_slot[k - k0] = k;
+      }
+      p.store = A;
+      p.wstore = Wst;
+      if ((rc = launch(0, p))) return rc;
+      pos = seg_end;
+      k0 = k1;
+    } while (pos < L - 1);
+  }
+  // forward statistic pass 2 (mismatches), read at the last locus
+  {
+    lsk::PropParams p;
+    base_params(ctx, p, 0);
+    p.l_first = 0;
+    p.n_steps = L;
+    p.init = 1;
+    p.tab_t0 = t_from;
+    p.state_rows = T;
+    p.eta = eta[0];
+    p.eta_vec = ctx->mu_vec ? d_eta : nullptr;
+    p.stat_out = EM;
+    if ((rc = launch(1, p))) return rc;
+  }
+  // backward: beta at the group ends (decreasing), in launches of at most kMaxStore stores
+  if (G > 0) {
+    int k0 = 0, pos = L;  // stores are taken in the order e_{G-1}, ..., e_0
+    do {
+      const int k1 = std::min(G, k0 + lsk::kMaxStore);
+      const int seg_end = ge[G - k1];  // the lowest store locus of this launch
+      lsk::PropParams p;
+      base_params(ctx, p, 1);
+      p.l_first = pos == L ? L - 1 : pos;
+      p.n_steps = p.l_first - seg_end + 1;
+      p.init = pos == L ? 1 : 0;
+      p.load_state = pos == L ? 0 : 1;
+      p.save_state = 1;
+      p.tab_t0 = t_from;
+      p.state_rows = T;
+      p.state = xst;
+      p.n_store = k1 - k0;
+      for (int k = k0; k < k1; ++k) {
+        p.store_loci[k - k0] = ge[G - 1 - k];
+        p.store_slot[k - k0] = G - 1 - k;
+      }
+      p.store = B;
+      if ((rc = run_launches(ctx, p, t_from, T, s))) return rc;
+      pos = seg_end;
+      k0 = k1;
+    } while (k0 < G);
+    lsk::grad_dot_kernel<<<dim3(T, G), 256, 0, s>>>(A, Wst, B, N, T, Rg);
+    CUDA_TRY(cudaGetLastError());
+    lsk::sum_rows_kernel<<<G, 256, 0, s>>>(Rg, T, sums);
+    CUDA_TRY(cudaGetLastError());
+  }
+  lsk::sum_rows_kernel<<<1, 256, 0, s>>>(EM, T, sums + G);
+  CUDA_TRY(cudaGetLastError());
+  lsk::sum_rows_kernel<<<1, 256, 0, s>>>(logF, T, sums + G + 1);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> hs(G + 2);
+  std::vector<uint32_t> sh(T);
+  CUDA_TRY(cudaMemcpyAsync(hs.data(), sums, sizeof(double) * (G + 2), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(sh.data(), stat, sizeof(uint32_t) * T, cudaMemcpyDeviceToHost, s));
+  if ((rc = read_err_word(ctx, s))) return rc;
+  // constant terms of the scores, FP64 on the host
+  if (dlogrho_out) {
+    for (int k = 0; k < K; ++k) dlogrho_out[k] = 0.0;
+    std::vector<double> cst(K, 0.0);
+    for (int m = 0; m + 1 < L; ++m) cst[interval_of[m]] += ctx->rho_h[m] / (1.0 - ctx->rho_h[m]);
+    for (int g = 0; g < G; ++g) dlogrho_out[gk[g]] = hs[g] - (double)T * cst[gk[g]];
+  }
+  if (dlogmu_out) {
+    double cm = 0.0;
+    for (int l = 0; l < L; ++l) {
+      const double m = ctx->mu_h[ctx->mu_h.size() > 1 ? l : 0];
+      cm += m / (1.0 - m);
+    }
+    *dlogmu_out = hs[G] - (double)T * cm;
+  }
+  if (pac_out) *pac_out = hs[G + 1];
+  uint32_t any = 0;
+  for (auto v : sh) any |= v;
+  if (any & 1u) return LS_WARN_UNDERFLOW;
+  if (any & 2u) return LS_WARN_OVERFLOW;
+  return LS_OK;
+}
+
 int ls_set_profiling(ls_ctx* ctx, int32_t enable) {
   int rc = check_ctx(ctx);
   if (rc) return rc;
@@ -995,7 +1233,7 @@ int plan_fixed(ls_ctx* c, int t_count, Launch* out, int* nout) {
   int nc = 0;
   for (const auto& k : registry()) {
     if (nc >= 64) break;
-    if (k.pim != (c->Pi ? 1 : 0) || !k.serves(c->N)) continue;
+    if (k.st != 0 || k.pim != (c->Pi ? 1 : 0) || !k.serves(c->N)) continue;
     const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;
     bool ok = true;

@@ -180,4 +180,48 @@ __global__ void ckpt_decode_f16_kernel(const __half* __restrict__ q, const float
   for (int j = threadIdx.x; j < N; j += blockDim.x) x[j] = __half2float(qr[j]) * sc;
 }
 
+// Adjoint: per (group g, target t) the posterior expectation of a statistic at the group's end
+// locus, sum_j w_j beta_j / sum_j alpha_j beta_j, from the stored alpha, w and beta rows.  FP32
+// products, FP64 sums.  grid (T, G), 256 threads.
+__global__ void grad_dot_kernel(const float* __restrict__ A, const float* __restrict__ Wst, const float* __restrict__ B,
+                                int N, int T, double* __restrict__ out) {
+  __shared__ double sa[256], sw[256];
+  const size_t row = (size_t)blockIdx.y * T + blockIdx.x;
+  const float* a = A + row * N;
+  const float* w = Wst + row * N;
+  const float* b = B + row * N;
+  double da = 0.0, dw = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const float bj = b[j];
+    da += (double)(a[j] * bj);
+    dw += (double)(w[j] * bj);
+  }
+  sa[threadIdx.x] = da;
+  sw[threadIdx.x] = dw;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sa[threadIdx.x] += sa[threadIdx.x + h];
+      sw[threadIdx.x] += sw[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[row] = sw[0] / sa[0];
+}
+
+// Fixed-order FP64 sums of `rows` vectors of length n (one block of 256 threads per row).
+__global__ void sum_rows_kernel(const double* __restrict__ v, int n, double* __restrict__ out) {
+  __shared__ double s[256];
+  const double* r = v + (size_t)blockIdx.x * n;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) acc += r[j];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = s[0];
+}
+
 }  // namespace lsk

@@ -13,6 +13,7 @@
 struct PropKernelInfo {
   int tpw, w, kq;
   int pim;  // 1: prior-matrix variant
+  int st;   // 1: statistic-pass variant (launch's dir argument picks ST 1 or ST 2)
   const void* func[2];
   cudaError_t (*launch)(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s);
   int (*smem_bytes)(int rw2);
@@ -39,6 +40,7 @@ struct ls_ctx {
   float* Pi = nullptr;            // [N][N] prior matrix copy (null: uniform)
   float pi_u = 0.0f;
   int mu_vec = 0;                 // mu given per locus
+  std::vector<double> rho_h, mu_h;  // host copies (the gradient's constant terms)
   // scratch
   double* logs_scratch = nullptr; // [N]
   uint32_t* status_scratch = nullptr;  // [N]

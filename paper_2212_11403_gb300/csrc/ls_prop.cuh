@@ -68,6 +68,14 @@ struct PropParams {
   float* store;           // [slots][state_rows][N] alpha (fwd) / beta (bwd) at store loci
   float* alpha_dec;       // backward decode: alpha at the same loci, same layout (may be null);
                           // overwritten in place by alpha * beta (normalised by decode_kernel)
+  // forward statistic passes (ST > 0): w_j = alpha_j E[S | Z = j, h_0..l] for an additive S
+  const float* gam;       // [L-1] weight of a recombination at interval m (ST 1)
+  const uint8_t* reset;   // [L-1] 1: interval m opens a new group, w restarts from 0 (ST 1)
+  float eta;              // weight of a mismatch emission, eta = 1/(1-mu) (ST 2, scalar mu)
+  const float* eta_vec;   // [L] per-locus eta (ST 2, mu varying per locus)
+  float* wstore;          // [slots][state_rows][N] w at the store loci (ST 1), may be null
+  float* wstate;          // [state_rows][N] w carried between launches
+  double* stat_out;       // [state_rows] sum w / sum alpha after the last step (ST 2)
   int* err;               // device error word (timeouts), may be null
 };
 
@@ -169,7 +177,7 @@ struct PropCfg {
   // timeout flag, TMA ring, store/load staging (the emission tables are static shared memory)
   static constexpr int BAR_OFF = 0;
   static constexpr int PART_OFF = BAR_OFF + kSlots * 8;
-  static constexpr int LOGR_OFF = PART_OFF + 2 * TPW * W * 4;
+  static constexpr int LOGR_OFF = PART_OFF + 2 * TPW * W * 8;  // two buffers of float2 partials
   static constexpr int LOG_OFF = ((LOGR_OFF + TPW * 32 * 4 + 7) / 8) * 8;
   static constexpr int ST_OFF = LOG_OFF + TPW * 8;
   static constexpr int FLAG_OFF = ST_OFF + TPW * 4;
@@ -202,8 +210,16 @@ __host__ __device__ __forceinline__ void slice_of(int sigma, int S, int N, int& 
 // PIM = 1: prior matrix.  Each lane keeps its slots' prior values pi_j (zero on padding and on
 // the diagonal) in shared memory; the forward adds rho * pi_j per cell and the backward sums
 // t_j pi_j, so no junk correction is needed.
-template <int DIR, int TPW, int W, int KQ, int PIM>
-__global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kernel(const PropParams p) {
+//
+// ST > 0 (forward, uniform prior): a second register tile w carries w_j = alpha_j tau_j, tau_j the
+// filtered expectation of an additive statistic S given copying state j.  With S_{l+1} = S_l +
+// gamma_l B_l + eta H_{l+1}(Z_{l+1}) (B_l the recombination event of interval l, H the mismatch
+// indicator) the recursion is the forward one plus a source:
+//   w_j <- theta_j (c w_j + r (W/s + gamma)) + eta H_j x_j,   W = sum_j w_j, s = sum_j x_j.
+// ST 1 takes the recombination term (restarted at every group of intervals), ST 2 the mismatch term.
+template <int DIR, int TPW, int W, int KQ, int PIM, int ST>
+__global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_prop_kernel(const PropParams p) {
+  static_assert(ST == 0 || (DIR == 0 && PIM == 0), "statistic passes run forward with the uniform prior");
   using C = PropCfg<TPW, W, KQ>;
   constexpr int SPW = C::SPW, S = C::S, NWORD = C::NWORD, THREADS = C::THREADS;
   constexpr int step_dir = DIR == 0 ? 1 : -1;
@@ -221,6 +237,8 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
   // indexed by 16 x (4 match bits); static so the table's address folds into the load offset
   __shared__ __align__(256) float s_lut[2][64];
   float* lutf = &s_lut[0][0];
+  // ST 2: eta H for the same 16 x 4 entries (0 on a match, eta on a mismatch)
+  __shared__ __align__(256) float s_hlut[ST == 2 ? 2 : 1][ST == 2 ? 64 : 4];
   uint32_t* ring = reinterpret_cast<uint32_t*>(smem + lay.ring_off);
   float* stg = reinterpret_cast<float*>(smem + lay.stg_off);
 
@@ -292,6 +310,7 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
   if (tid < 64) {
     const int e = tid >> 2, k = tid & 3;
     lutf[tid] = ((e >> k) & 1) ? p.thm[p.l_first] : p.thx[p.l_first];
+    if (ST == 2) s_hlut[0][tid] = ((e >> k) & 1) ? 0.0f : (p.eta_vec ? p.eta_vec[p.l_first] : p.eta);
   }
   if (tid < TPW) {
     lgs[tid] = (o + tid < p.t_begin + p.t_count && p.logs && !p.init) ? p.logs[o + tid - p.tab_t0] : 0.0;
@@ -303,24 +322,38 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
 
   // ---- the register tile ------------------------------------------------------------------
   f2 x[KQ][2];
+  f2 wv[ST ? KQ : 1][2];  // statistic tile (ST > 0)
 #pragma unroll
   for (int k = 0; k < KQ; ++k) x[k][0] = x[k][1] = make_float2(0.f, 0.f);
-  if (p.load_state) {
+#pragma unroll
+  for (int k = 0; k < (ST ? KQ : 1); ++k) wv[k][0] = wv[k][1] = make_float2(0.f, 0.f);
+  auto load_tile = [&](f2 (&v)[ST ? KQ : 1][2], f2 (&u)[KQ][2], bool into_w, const float* src) {
 #pragma unroll
     for (int c = 0; c < C::NCHUNK; ++c) {
-      xfer(c, p.state, 0, false);
+      xfer(c, const_cast<float*>(src), 0, false);
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int k = 8 * c + q;
         if (k < KQ) {
-          const float4 v = *reinterpret_cast<const float4*>(stg + tid * C::STG_STRIDE + 4 * q);
-          x[k][0] = make_float2(v.x, v.y);
-          x[k][1] = make_float2(v.z, v.w);
+          const float4 t4 = *reinterpret_cast<const float4*>(stg + tid * C::STG_STRIDE + 4 * q);
+          if (into_w) {
+            if (ST) {
+              v[ST ? k : 0][0] = make_float2(t4.x, t4.y);
+              v[ST ? k : 0][1] = make_float2(t4.z, t4.w);
+            }
+          } else {
+            u[k][0] = make_float2(t4.x, t4.y);
+            u[k][1] = make_float2(t4.z, t4.w);
+          }
         }
       }
       __syncthreads();
     }
+  };
+  if (p.load_state) {
+    load_tile(wv, x, false, p.state);
+    if (ST) load_tile(wv, x, true, p.wstate);
   }
   // prior values of this lane's slots (matrix prior): slot s <-> donor (start + s + o) mod N
   const float* pis = reinterpret_cast<const float*>(smem + lay.pi_off) + tid * C::PI_STRIDE;
@@ -339,7 +372,7 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
   }
 
   // store the tile (mode 0: x; 1: c x + r; 2: multiply the destination by c x + r)
-  auto store_tile = [&](float* gbase, int mode, float c, float r) {
+  auto store_tile = [&](float* gbase, int mode, float c, float r, bool from_w = false) {
     const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
 #pragma unroll
     for (int cc = 0; cc < C::NCHUNK; ++cc) {
@@ -347,8 +380,10 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
       for (int q = 0; q < 8; ++q) {
         const int k = 8 * cc + q;
         if (k < KQ) {
-          const f2 a = mode == 0 ? x[k][0] : __ffma2_rn(C2, x[k][0], R2);
-          const f2 b = mode == 0 ? x[k][1] : __ffma2_rn(C2, x[k][1], R2);
+          const f2 xa = (ST && from_w) ? wv[ST ? k : 0][0] : x[k][0];
+          const f2 xb = (ST && from_w) ? wv[ST ? k : 0][1] : x[k][1];
+          const f2 a = mode == 0 ? xa : __ffma2_rn(C2, xa, R2);
+          const f2 b = mode == 0 ? xb : __ffma2_rn(C2, xb, R2);
           *reinterpret_cast<float4*>(stg + tid * C::STG_STRIDE + 4 * q) = make_float4(a.x, a.y, b.x, b.y);
         }
       }
@@ -361,16 +396,29 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
   float sig_prev = 1.0f;  // previous normaliser (fwd: sum alpha; bwd: S)
   float xs = 0.0f;        // common value of the junk cells
 
-  // reduce one value per lane over the layout; returns the CTA total for target tl
-  auto reduce = [&](float v, float* buf) -> float {
+  // reduce one value (or, with ST, a pair) per lane over the layout; CTA totals for target tl
+  auto reduce2 = [&](float v, float u, float* buf, float& tu) -> float {
 #pragma unroll
-    for (int off = TPW; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (sl == 0) buf[tl * W + warp] = v;
+    for (int off = TPW; off < 32; off <<= 1) {
+      v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (ST) u += __shfl_xor_sync(0xffffffffu, u, off);
+    }
+    float2* b2 = reinterpret_cast<float2*>(buf);
+    if (sl == 0) b2[tl * W + warp] = make_float2(v, u);
     __syncthreads();
     float t = 0.0f;
+    tu = 0.0f;
 #pragma unroll
-    for (int w = 0; w < W; ++w) t += buf[tl * W + w];
+    for (int w = 0; w < W; ++w) {
+      const float2 e = b2[tl * W + w];
+      t += e.x;
+      tu += e.y;
+    }
     return t;
+  };
+  auto reduce = [&](float v, float* buf) -> float {
+    float dummy;
+    return reduce2(v, 0.0f, buf, dummy);
   };
   // fold the log ring into the FP64 log scales (warp 0; entries 0..cnt-1) and check the normalisers
   auto flush_logs = [&](int cnt) {
@@ -394,11 +442,17 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
     __syncwarp();
   };
 
+  float wsum_prev = 0.0f;  // ST: sum of w over the real donors
+  float ws = 0.0f;        // ST: common value of w in the junk cells
   if (p.load_state && DIR == 0) {
-    float s = 0.0f;
+    float s = 0.0f, sw = 0.0f;
 #pragma unroll
     for (int k = 0; k < KQ; ++k) s += (x[k][0].x + x[k][0].y) + (x[k][1].x + x[k][1].y);
-    sig_prev = reduce(s, part + TPW * W);
+    if (ST) {
+#pragma unroll
+      for (int k = 0; k < (ST ? KQ : 1); ++k) sw += (wv[k][0].x + wv[k][0].y) + (wv[k][1].x + wv[k][1].y);
+    }
+    sig_prev = reduce2(s, sw, part + 2 * TPW * W, wsum_prev);
     __syncthreads();
   }
 
@@ -439,6 +493,7 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
     const uint32_t* rw = slot_rows + (l - blk_base) * rw2;
 
     float c, r;
+    float cw = 0.0f, rws = 0.0f;  // ST: coefficients of the w recursion
     bool add_log_prev = false;
     if (step == 0 && p.init) {
       c = 0.0f;
@@ -450,11 +505,23 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
       c = __fdividef(cur_omr, sig_prev);  // interval l-1 (fwd) or l (bwd); 2-ulp reciprocal-multiply
       r = cur_rr;
       add_log_prev = DIR == 1;
+      if (ST) {
+        const float wbar = __fdividef(wsum_prev, sig_prev);  // W / s = E[S_l | h_0..l]
+        if (ST == 1) {
+          const bool rs = p.reset[l - 1] != 0;
+          cw = rs ? 0.0f : c;
+          rws = r * ((rs ? 0.0f : wbar) + p.gam[l - 1]);
+        } else {
+          cw = c;
+          rws = r * wbar;
+        }
+      }
     }
     const bool is_store = l == next_store_l;
     const bool save_here = p.save_state && step == p.n_steps - 1;
     if (DIR == 0 && pend_slot >= 0) {  // alpha of the previous locus
       store_tile(p.store + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f);
+      if (ST && p.wstore) store_tile(p.wstore + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f, true);
       pend_slot = -1;
     }
 
@@ -471,7 +538,9 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
     const uint32_t inv = ((rw[abit >> 5] >> (abit & 31)) & 1u) ? 0u : 0xffffffffu;  // target allele
     const uint32_t lut_b = p.mu_vec ? (uint32_t)((step & 1) << 8) : 0u;  // byte offset of this step's table
     const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
+    const f2 CW2 = make_float2(cw, cw), RW2 = make_float2(rws, rws);
     f2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    f2 accw0 = make_float2(0.f, 0.f), accw1 = make_float2(0.f, 0.f);
     // Software pipeline: the emission-table entries are loaded kLA quads ahead of their use from a
     // rotating register buffer; a slice word's nibbles are prepared when the lookahead enters it.
     constexpr int kLA = KQ < 4 ? KQ : 4;
@@ -526,9 +595,30 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
         x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
         acc0 = __fadd2_rn(acc0, x[k][0]);
         acc1 = __fadd2_rn(acc1, x[k][1]);
+        if (ST) {
+          const int kw = ST ? k : 0;
+          const f2 v01 = __fmul2_rn(make_float2(t.x, t.y), __ffma2_rn(CW2, wv[kw][0], RW2));
+          const f2 v23 = __fmul2_rn(make_float2(t.z, t.w), __ffma2_rn(CW2, wv[kw][1], RW2));
+          if (ST == 2) {  // + eta H x (the emission term of the mismatch statistic)
+            const int q = k & 7, m = k >> 3;
+            const uint32_t off = __byte_perm((q & 1) ? hw[m & 1] : lw[m & 1], lut_b, 0x7650u | (uint32_t)(q >> 1));
+            const float4 hv = *reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(s_hlut) + off);
+            wv[kw][0] = __ffma2_rn(make_float2(hv.x, hv.y), x[k][0], v01);
+            wv[kw][1] = __ffma2_rn(make_float2(hv.z, hv.w), x[k][1], v23);
+          } else {
+            wv[kw][0] = v01;
+            wv[kw][1] = v23;
+          }
+          accw0 = __fadd2_rn(accw0, wv[kw][0]);
+          accw1 = __fadd2_rn(accw1, wv[kw][1]);
+        }
       }
     }
     xs = cur_thx * fmaf(c, xs, r);  // junk cells: theta = mu in every lane
+    if (ST) {  // the same operations as a mismatch cell
+      const float v = __fmul_rn(cur_thx, __fmaf_rn(cw, ws, rws));
+      ws = ST == 2 ? __fmaf_rn(p.eta_vec ? p.eta_vec[l] : p.eta, xs, v) : v;
+    }
 
     if (DIR == 0) {  // alpha^l is stored at the top of the next step (or after the loop)
       pend_slot = is_store && p.store ? p.store_slot[store_next] : -1;
@@ -543,9 +633,13 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
     if (p.mu_vec && tid < 64 && step + 1 < p.n_steps) {
       const int e = tid >> 2, k = tid & 3;
       lutf[((step + 1) & 1) * 64 + tid] = ((e >> k) & 1) ? nx_thm : nx_thx;
+      if (ST == 2) s_hlut[(step + 1) & 1][tid] = ((e >> k) & 1) ? 0.0f : p.eta_vec[l + 1];
     }
 
-    const float tot = reduce((acc0.x + acc0.y) + (acc1.x + acc1.y), part + (step & 1) * TPW * W);
+    float wtot = 0.0f;
+    const float tot = reduce2((acc0.x + acc0.y) + (acc1.x + acc1.y), (accw0.x + accw0.y) + (accw1.x + accw1.y),
+                              part + (step & 1) * 2 * TPW * W, wtot);
+    if (ST) wsum_prev = wtot - n_junk * ws;
     float sig = tot - n_junk * xs;
     if (DIR == 1 && !PIM) sig *= p.pi_u;
     if (tid < TPW) lgr[tid * 32 + (step & 31)] = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
@@ -554,13 +648,20 @@ __global__ void __launch_bounds__(W * 32, (PIM && W >= 8) ? 1 : 2) ls_prop_kerne
   }
 
   if (DIR == 0) {
-    if (pend_slot >= 0) store_tile(p.store + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f);
-    if (pend_save) store_tile(p.state, 0, 0.f, 0.f);
+    if (pend_slot >= 0) {
+      store_tile(p.store + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f);
+      if (ST && p.wstore) store_tile(p.wstore + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f, true);
+    }
+    if (pend_save) {
+      store_tile(p.state, 0, 0.f, 0.f);
+      if (ST) store_tile(p.wstate, 0, 0.f, 0.f, true);
+    }
   }
   if (tid < TPW && o + tid < p.t_begin + p.t_count) {
     const int row = o + tid - p.tab_t0;
     const uint32_t stb = sts[tid] | (*flag ? 4u : 0u);  // 4 = LS_STATUS_TIMEOUT
     if (p.logs) p.logs[row] = lgs[tid];
+    if (ST && p.stat_out) p.stat_out[row] = (double)wsum_prev / (double)sig_prev;
     if (p.status && stb) atomicOr(p.status + row, stb);
     if (*flag && p.err) atomicOr(p.err, 1);
   }

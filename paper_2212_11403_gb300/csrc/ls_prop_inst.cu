@@ -10,8 +10,16 @@ namespace {
 
 template <int TPW, int W, int KQ, int PIM>
 cudaError_t launch_prop(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
-  if (dir == 0) lsk::ls_prop_kernel<0, TPW, W, KQ, PIM><<<grid, W * 32, smem, s>>>(p);
-  else lsk::ls_prop_kernel<1, TPW, W, KQ, PIM><<<grid, W * 32, smem, s>>>(p);
+  if (dir == 0) lsk::ls_prop_kernel<0, TPW, W, KQ, PIM, 0><<<grid, W * 32, smem, s>>>(p);
+  else lsk::ls_prop_kernel<1, TPW, W, KQ, PIM, 0><<<grid, W * 32, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// statistic passes (forward only): dir selects ST 1 (0) or ST 2 (1)
+template <int TPW, int W, int KQ>
+cudaError_t launch_stat(int which, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
+  if (which == 0) lsk::ls_prop_kernel<0, TPW, W, KQ, 0, 1><<<grid, W * 32, smem, s>>>(p);
+  else lsk::ls_prop_kernel<0, TPW, W, KQ, 0, 2><<<grid, W * 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -28,11 +36,17 @@ bool serves_prop(int N) {
 }  // namespace
 
 #define LS_REGP(T, Wp, K, P)                                                                        \
-  out.push_back(PropKernelInfo{T, Wp, K, P,                                                         \
-                               {(const void*)lsk::ls_prop_kernel<0, T, Wp, K, P>,                   \
-                                (const void*)lsk::ls_prop_kernel<1, T, Wp, K, P>},                  \
+  out.push_back(PropKernelInfo{T, Wp, K, P, 0,                                                      \
+                               {(const void*)lsk::ls_prop_kernel<0, T, Wp, K, P, 0>,                \
+                                (const void*)lsk::ls_prop_kernel<1, T, Wp, K, P, 0>},               \
                                launch_prop<T, Wp, K, P>, smem_prop<T, Wp, K, P>, serves_prop<T, Wp, K>})
 #define LS_REG(T, Wp, K) LS_REGP(T, Wp, K, 0)
+// statistic-pass variants: func[0] = ST 1, func[1] = ST 2
+#define LS_REGS(T, Wp, K)                                                                           \
+  out.push_back(PropKernelInfo{T, Wp, K, 0, 1,                                                      \
+                               {(const void*)lsk::ls_prop_kernel<0, T, Wp, K, 0, 1>,                \
+                                (const void*)lsk::ls_prop_kernel<0, T, Wp, K, 0, 2>},               \
+                               launch_stat<T, Wp, K>, smem_prop<T, Wp, K, 0>, serves_prop<T, Wp, K>})
 
 #if LS_INST_GROUP == 0
 void ls_register_group0(std::vector<PropKernelInfo>& out) {
@@ -88,5 +102,16 @@ void ls_register_group7(std::vector<PropKernelInfo>& out) {
   LS_REGP(1, 4, 40, 1);
   LS_REGP(1, 8, 20, 1);
   LS_REGP(8, 4, 16, 1);
+}
+#elif LS_INST_GROUP == 8
+void ls_register_group8(std::vector<PropKernelInfo>& out) {
+  // statistic passes of the adjoint (uniform prior), one target per CTA
+  LS_REGS(1, 4, 1);
+  LS_REGS(1, 4, 8);
+}
+#elif LS_INST_GROUP == 9
+void ls_register_group9(std::vector<PropKernelInfo>& out) {
+  LS_REGS(1, 4, 16);
+  LS_REGS(1, 4, 20);
 }
 #endif

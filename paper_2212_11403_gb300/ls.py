@@ -42,7 +42,7 @@ EXPORTED = [
     "ls_export_packed", "ls_calc_rho", "ls_set_params", "ls_table_create", "ls_table_destroy", "ls_table_copy",
     "ls_table_reset", "ls_table_info", "ls_table_read", "ls_forward", "ls_backward", "ls_posterior", "ls_distance",
     "ls_checkpoints", "ls_ckpt_info", "ls_ckpt_read", "ls_ckpt_replay", "ls_ckpt_destroy",
-    "ls_run_all", "ls_run_all_noalloc", "ls_set_profiling", "ls_profile_read",
+    "ls_run_all", "ls_run_all_noalloc", "ls_pac_grad", "ls_set_profiling", "ls_profile_read",
 ]
 
 
@@ -86,6 +86,7 @@ def _load():
         "ls_distance": ([P, P, P, P, P], I),
         "ls_run_all": ([P, P, I, P, P, P, P], I),
         "ls_run_all_noalloc": ([P, P, I, P, P, P, P], I),
+        "ls_pac_grad": ([P, I, I, P, I, P, P, P, P], I),
         "ls_set_profiling": ([P, I], I),
         "ls_profile_read": ([P, P, P], I),
     }
@@ -312,6 +313,20 @@ def ls_run_all_noalloc(ctx, decode_loci, d_out, want_pac=True, status_out=None, 
                                         _dev(d_out, torch.float32, "d_out"), ctypes.byref(pac) if want_pac else None,
                                         _dev(status_out, torch.int32, "status"), _stream(stream)))
     return rc, (pac.value if want_pac else None)
+
+
+def ls_pac_grad(ctx, interval_of, K, t_from=0, t_to=None, stream=None):
+    """PAC log-likelihood of targets [t_from, t_to) and its gradient: returns
+    (rc, pac, dlogmu, dlogrho [K] float64)."""
+    io = np.ascontiguousarray(interval_of, dtype=np.int32)
+    if t_to is None:
+        t_to = ls_info(ctx)["N"]
+    pac, gm = ctypes.c_double(), ctypes.c_double()
+    gr = np.zeros(int(K), dtype=np.float64)
+    rc = _check(_lib.ls_pac_grad(ctx, int(t_from), int(t_to), io.ctypes.data_as(ctypes.c_void_p) if io.size else None,
+                                 int(K), ctypes.byref(pac), ctypes.byref(gm), gr.ctypes.data_as(ctypes.c_void_p),
+                                 _stream(stream)))
+    return rc, pac.value, gm.value, gr
 
 
 def ls_set_profiling(ctx, enable=True):
