@@ -6,7 +6,8 @@ Tolerance.  Each group gradient is a difference of two terms of similar size: th
 expectation sum_i E[sum_m B_m / (1-rho_m)] (computed in FP32 per target, summed in FP64) and the
 constant T sum_m rho_m / (1-rho_m).  Its error is held to 1e-5 of the magnitude of those terms:
 the per-target expectations are FP32 recursions over up to L loci (relative error about 1e-6
-at L = 10000); the same form is used for d/dlog mu.  The PAC log-likelihood uses the log tolerance of the parity tests.
+at L = 10000); the same form is used for d/dlog mu.  The PAC log-likelihood uses the log
+tolerance of the parity tests.
 """
 import math
 
@@ -177,3 +178,19 @@ def test_pac_grad_n10000_l10000_sampled_targets(ls):
     ref = oracle.pac_grad(w["h"], w["rho"], w["mu"], iv, K, targets=targets, nthreads=4)
     e = check_grad(pac, gm, gr, ref, w["rho"], w["mu"], L, iv, K, 16, N)
     print("\nN=L=10000 K=100 16 targets: max group err %.2e, mu err %.2e" % e)
+    h = 1e-4
+
+    def pac_at(dlmu=0.0, k=None, d=0.0):
+        rho = w["rho"].copy()
+        if k is not None:
+            rho[iv == k] *= math.exp(d)
+        r = oracle.run(w["h"], rho, w["mu"] * math.exp(dlmu), [0], targets=targets, want=("llf",))
+        return float(r["llf"].sum())
+
+    cr, cm = magnitudes(w["rho"], w["mu"], L, iv, K, 16)
+    fd_tol = 1e-12 * abs(pac) / h
+    fd_mu = (pac_at(dlmu=h) - pac_at(dlmu=-h)) / (2 * h)
+    assert abs(gm - fd_mu) <= G_RTOL * (abs(fd_mu) + cm) + fd_tol, (gm, fd_mu)
+    for k in (3, 71):
+        fd = (pac_at(k=k, d=h) - pac_at(k=k, d=-h)) / (2 * h)
+        assert abs(gr[k] - fd) <= G_RTOL * (abs(fd) + cr[k]) + fd_tol, (k, gr[k], fd)
