@@ -57,6 +57,7 @@ typedef void* ls_stream_t; /* a cudaStream_t */
 typedef struct ls_ctx ls_ctx;
 typedef struct ls_table ls_table;
 typedef struct ls_ckpt ls_ckpt;
+typedef struct ls_mlp ls_mlp;
 
 /* Library version and build description (arch, kernel variants).  Static string. */
 const char* ls_version(void);
@@ -221,6 +222,71 @@ int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out,
  * Returns LS_WARN_* like ls_run_all. */
 int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interval_of, int32_t K,
                 double* pac_out, double* dlogmu_out, double* dlogrho_out, ls_stream_t stream);
+
+/* ---- learned sparse path: donor proposal, MLP, restricted recursions ------------------------
+ * The paper runs every target against all N-1 donors.  This extension restricts target i in
+ * window w (256 consecutive loci) to a proposed set S_i^w of K donors: stage 1 keeps the C donors
+ * with the fewest mismatches over windows w-1..w+1, stage 2 scores them with a 3-layer MLP
+ * (8 -> 256 -> 256 -> 1, ReLU) on the match fractions of windows w-3..w+3 and keeps the K best.
+ * The recursions of Eq. fwd1 / Eq. bck1 then run over the sets (prior 1/(N-1) as in the dense
+ * chain, recombination mass to donors outside the set dropped, continuation only for donors kept
+ * across a window change), and targets whose forward mass leaves the sets are recomputed
+ * densely. */
+
+/* Posterior rows (Eq. postprob) from caller-held alpha and beta rows of targets
+ * [t_from, t_from+T): p_out device float [T][N].  Enqueued on stream. */
+int ls_posterior_rows(ls_ctx* ctx, const float* alpha, const float* beta, int32_t t_from, int32_t T, float* p_out,
+                      ls_stream_t stream);
+
+/* Network parameters as one FP32 vector of LS_MLP_PARAMS floats: W1 [8][256] (input x unit; the
+ * eighth input is always 0), b1 [256], W2 [256][256], b2 [256], w3 [256], b3.  params NULL gives
+ * a He-uniform initialisation from seed.  The network lives on the current device. */
+#define LS_MLP_PARAMS 68353
+int ls_mlp_create(const float* params, uint64_t seed, ls_mlp** out);
+int ls_mlp_destroy(ls_mlp* m);
+int ls_mlp_get(const ls_mlp* m, float* params);
+int ls_mlp_set(ls_mlp* m, const float* params);
+
+/* Scores of n feature rows X (device float [n][8]) by the BF16 tensor-core inference kernel
+ * (weights and hidden activations rounded to BF16, FP32 accumulation): scores device float [n].
+ * Synchronous. */
+int ls_mlp_forward(const ls_mlp* m, const float* X, int64_t n, float* scores, ls_stream_t stream);
+
+/* FP32 gradient of the loss sum_r (s_r - y_r)^2 / (2n) over n rows (X [n][8], y [n], device) at
+ * the current parameters: grad host float [LS_MLP_PARAMS] (may be NULL), loss host double.
+ * Synchronous. */
+int ls_mlp_grad(ls_mlp* m, const float* X, const float* y, int32_t n, float* grad, double* loss, ls_stream_t stream);
+
+/* `steps` Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) on minibatches of `batch` rows drawn
+ * with replacement by a seeded splitmix64 stream; loss_out = mean minibatch loss over the last
+ * tenth of the steps.  Synchronous. */
+int ls_mlp_train(ls_mlp* m, const float* X, const float* y, int64_t n, int32_t steps, int32_t batch, float lr,
+                 uint64_t seed, double* loss_out, ls_stream_t stream);
+
+/* Stage 1 of window w alone: cand_out device int32 [N][C] (ascending ids, -1 padding) and, if not
+ * NULL, feat_out device float [N][C][8] (match fractions of windows w-3..w+3, then 0).
+ * Synchronous. */
+int ls_propose_window(ls_ctx* ctx, int32_t C, int32_t w, int32_t* cand_out, float* feat_out, ls_stream_t stream);
+
+/* Donor sets for every window: idx_out device int32 [N][ceil(L/256)][K] in ascending id order.
+ * With mlp NULL the K donors are stage 1's (C ignored); otherwise stage 1 keeps C (K <= C <= 2048)
+ * and the network keeps the K best scores (ties to the lower id).  1 <= K <= 512.  Synchronous. */
+int ls_propose(ls_ctx* ctx, int32_t C, int32_t K, const ls_mlp* mlp, int32_t* idx_out, ls_stream_t stream);
+
+/* Sparse forward + backward over donor sets idx (device int32 [N][ceil(L/WS)][K], ascending ids,
+ * -1 padding, never the target itself), posteriors and distances at the D decode loci.  Window w
+ * runs on S^w (lookahead 0), S^w u S^{w+1} (1: every proposed donor has a window of history when
+ * its own window starts) or S^{w-1} u S^w u S^{w+1} (2: proposed donors also stay a window
+ * longer); (lookahead + 1) K <= 1536.  d_out
+ * device float [D][N][N]: d_ij of Eq. distmat where j is in i's set and i in j's set at that
+ * locus' window, NaN elsewhere ("uncovered"), 0 on the diagonal.  Targets whose largest forward
+ * mass on donors leaving their set exceeds lost_tol (lost_tol < 0: never) get dense rows
+ * (requires N within the dense kernels' range); *n_fallback_out receives their number.
+ * lost_out device float [N] (may be NULL) receives that mass per target; pac_out the
+ * log-likelihood of the restricted chains.  Synchronous.  Uniform prior only. */
+int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, int32_t lookahead,
+                      const int32_t* decode_loci, int32_t D, float* d_out, float lost_tol, float* lost_out,
+                      double* pac_out, uint32_t* status_out, int32_t* n_fallback_out, ls_stream_t stream);
 
 /* ---- fused pipeline without allocation --------------------------------------------------- */
 

@@ -25,6 +25,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
 # (source, extra defines, object name)
 UNITS = [
     ("ls_api.cu", [], "ls_api.o"),
+    ("ls_sparse.cu", [], "ls_sparse.o"),
+    ("ls_propose.cu", [], "ls_propose.o"),
 ] + [("ls_prop_inst.cu", ["-DLS_INST_GROUP=%d" % g], "ls_prop_g%d.o" % g) for g in range(10)]
 
 

@@ -12,6 +12,8 @@
 
 #include "ls.h"
 #include "ls_aux.cuh"
+#define LS_SPARSE_PARAMS_ONLY
+#include "ls_sparse.cuh"
 #include "ls_internal.h"
 
 void ls_register_group0(std::vector<PropKernelInfo>& out);
@@ -281,6 +283,18 @@ bool is_device_ptr(const void* p) {
 }  // namespace
 
 // =============================================================================================
+int ls_fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int ls_dev_alloc(void** p, size_t bytes) { return dev_alloc(nullptr, p, bytes); }
+
 extern "C" {
 
 const char* ls_version(void) {
@@ -1133,6 +1147,190 @@ int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interv
   for (auto v : sh) any |= v;
   if (any & 1u) return LS_WARN_UNDERFLOW;
   if (any & 2u) return LS_WARN_OVERFLOW;
+  return LS_OK;
+}
+
+// ---- sparse recursions over proposed donor sets, with dense fallback ---------------------------
+}  // extern "C"
+
+namespace {
+// dense propagation of a list of targets (one target per CTA), for the fallback rows
+int run_list(ls_ctx* c, lsk::PropParams p, const int* d_tlist, int nf, cudaStream_t s) {
+  auto cs = candidates(c);
+  std::vector<Cand> one;
+  for (const auto& cd : cs)
+    if (cd.k->tpw == 1) one.push_back(cd);
+  if (one.empty()) return fail(LS_ERR_UNSUPPORTED, "no one-target propagation variant serves N=%d", c->N);
+  double cost = 0;
+  const Cand* b = best_for(one, nf, c->num_sms, &cost);
+  p.tlist = d_tlist;
+  p.t_begin = 0;
+  p.t_count = nf;
+  cudaError_t e = b->k->launch(p.dir, p, nf, b->smem, s);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, "fallback propagation launch: %s", cudaGetErrorString(e));
+  return LS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, int32_t lookahead,
+                      const int32_t* decode_loci, int32_t D, float* d_out, float lost_tol, float* lost_out,
+                      double* pac_out, uint32_t* status_out, int32_t* n_fallback_out, ls_stream_t stream) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
+  if (ctx->Pi) return fail(LS_ERR_UNSUPPORTED, "the sparse recursions support the uniform prior only");
+  const int N = ctx->N, L = ctx->L;
+  if (lookahead < 0 || lookahead > 2) return fail(LS_ERR_ARG, "lookahead must be 0, 1 or 2");
+  if (!idx || K < 1 || (lookahead + 1) * K > 1536)
+    return fail(LS_ERR_ARG, "need donor sets with 1 <= K and (lookahead + 1) K <= 1536 entries");
+  if (WS < 1) return fail(LS_ERR_ARG, "window size must be positive");
+  if (D < 1 || !decode_loci || !d_out) return fail(LS_ERR_ARG, "bad decode arguments");
+  if (D > lsk::kMaxStore) return fail(LS_ERR_UNSUPPORTED, "at most %d decode loci per call", lsk::kMaxStore);
+  for (int k = 0; k < D; ++k) {
+    if (decode_loci[k] < 0 || decode_loci[k] >= L) return fail(LS_ERR_ARG, "decode locus %d out of range", decode_loci[k]);
+    if (k && decode_loci[k] <= decode_loci[k - 1]) return fail(LS_ERR_ARG, "decode loci must be strictly increasing");
+  }
+  if (!is_device_ptr(idx) || !is_device_ptr(d_out)) return fail(LS_ERR_ARG, "idx and d_out must be device memory");
+  const int Wn = (L + WS - 1) / WS;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBufs db;
+  float *P, *lost;
+  double* logs;
+  uint32_t* stat;
+  int* wos;
+  if ((rc = db.get(&P, (size_t)D * N * K)) || (rc = db.get(&lost, N)) || (rc = db.get(&logs, N)) ||
+      (rc = db.get(&stat, N)) || (rc = db.get(&wos, D)))
+    return rc;
+  const int32_t* sets = idx;
+  if (lookahead) {  // run window w on S^w u S^{w+1} (and S^{w-1} with lookahead 2)
+    int32_t* U;
+    if ((rc = db.get(&U, (size_t)N * Wn * (lookahead + 1) * K))) return rc;
+    cudaError_t e0 = ls_launch_lookahead(idx, N, Wn, K, lookahead, U, s);
+    if (e0 != cudaSuccess) return fail(LS_ERR_CUDA, "lookahead sets: %s", cudaGetErrorString(e0));
+    sets = U;
+    K = (lookahead + 1) * K;
+    if ((rc = db.get(&P, (size_t)D * N * K))) return rc;  // the posteriors need the wider rows
+  }
+  std::vector<int> wh(D);
+  for (int k = 0; k < D; ++k) wh[k] = decode_loci[k] / WS;
+  CUDA_TRY(cudaMemcpyAsync(wos, wh.data(), sizeof(int) * D, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(uint32_t) * N, s));
+  lsk::SparseParams sp;
+  memset(&sp, 0, sizeof sp);
+  sp.bits = ctx->bits;
+  sp.row_words = ctx->row_words;
+  sp.N = N;
+  sp.L = L;
+  sp.K = K;
+  sp.WS = WS;
+  sp.Wn = Wn;
+  sp.idx = sets;
+  sp.omr = ctx->omr;
+  sp.rho = ctx->rr_b;
+  sp.thm = ctx->thm;
+  sp.thx = ctx->thx;
+  sp.t_begin = 0;
+  sp.t_count = N;
+  sp.store = P;
+  sp.status = stat;
+  sp.n_store = D;
+  for (int k = 0; k < D; ++k) {
+    sp.store_loci[k] = decode_loci[k];
+    sp.store_slot[k] = k;
+  }
+  sp.logs = logs;
+  sp.lost = lost;
+  cudaError_t e = ls_launch_sparse(0, sp, s);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, "sparse forward launch: %s", cudaGetErrorString(e));
+  for (int k = 0; k < D; ++k) {
+    sp.store_loci[k] = decode_loci[D - 1 - k];
+    sp.store_slot[k] = D - 1 - k;
+  }
+  sp.logs = nullptr;
+  sp.lost = nullptr;
+  e = ls_launch_sparse(1, sp, s);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, "sparse backward launch: %s", cudaGetErrorString(e));
+  // half distances of the covered entries; NaN (all bits set) elsewhere
+  CUDA_TRY(cudaMemsetAsync(d_out, 0xff, sizeof(float) * (size_t)D * N * N, s));
+  e = ls_launch_sparse_hdist(P, sets, N, K, Wn, wos, D, d_out, s);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, "sparse distance launch: %s", cudaGetErrorString(e));
+  std::vector<float> lh(N);
+  CUDA_TRY(cudaMemcpyAsync(lh.data(), lost, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
+  if (lost_out) CUDA_TRY(cudaMemcpyAsync(lost_out, lost, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int> fb;
+  if (lost_tol >= 0.0f)
+    for (int i = 0; i < N; ++i)
+      if (!(lh[i] <= lost_tol)) fb.push_back(i);
+  const int nf = (int)fb.size();
+  if (nf > 0) {
+    // dense rows of the targets whose set lost too much forward mass
+    int* tl;
+    float* prod;
+    if ((rc = db.get(&tl, nf)) || (rc = db.get(&prod, (size_t)D * nf * N))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(tl, fb.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, s));
+    lsk::PropParams p;
+    base_params(ctx, p, 0);
+    p.l_first = 0;
+    p.n_steps = L;
+    p.init = 1;
+    p.tab_t0 = 0;
+    p.state_rows = nf;
+    p.status = nullptr;
+    p.n_store = D;
+    for (int k = 0; k < D; ++k) {
+      p.store_loci[k] = decode_loci[k];
+      p.store_slot[k] = k;
+    }
+    p.store = prod;
+    if ((rc = run_list(ctx, p, tl, nf, s))) return rc;
+    base_params(ctx, p, 1);
+    p.l_first = L - 1;
+    p.n_steps = L;
+    p.init = 1;
+    p.tab_t0 = 0;
+    p.state_rows = nf;
+    p.n_store = D;
+    for (int k = 0; k < D; ++k) {
+      p.store_loci[k] = decode_loci[D - 1 - k];
+      p.store_slot[k] = D - 1 - k;
+    }
+    p.alpha_dec = prod;
+    if ((rc = run_list(ctx, p, tl, nf, s))) return rc;
+    e = ls_launch_dense_rows_hdist(prod, nf, N, tl, D, d_out, s);
+    if (e != cudaSuccess) return fail(LS_ERR_CUDA, "fallback distance launch: %s", cudaGetErrorString(e));
+  }
+  const int nt = (N + 31) / 32;
+  lsk::symmetrize_kernel<<<dim3(nt, nt, D), dim3(32, 8), 0, s>>>(d_out, N);
+  CUDA_TRY(cudaGetLastError());
+  if (status_out) CUDA_TRY(cudaMemcpyAsync(status_out, stat, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> lf(N);
+  std::vector<uint32_t> sh(N);
+  CUDA_TRY(cudaMemcpyAsync(lf.data(), logs, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(sh.data(), stat, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, s));
+  if ((rc = read_err_word(ctx, s))) return rc;
+  if (pac_out) {
+    double pac = 0.0;
+    for (int i = 0; i < N; ++i) pac += lf[i];
+    *pac_out = pac;
+  }
+  if (n_fallback_out) *n_fallback_out = nf;
+  uint32_t any = 0;
+  for (auto v : sh) any |= v;
+  if (any & 1u) return LS_WARN_UNDERFLOW;
+  if (any & 2u) return LS_WARN_OVERFLOW;
+  return LS_OK;
+}
+
+int ls_posterior_rows(ls_ctx* ctx, const float* alpha, const float* beta, int32_t t_from, int32_t T, float* p_out,
+                      ls_stream_t stream) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (!alpha || !beta || !p_out || T < 1 || t_from < 0 || t_from + T > ctx->N) return fail(LS_ERR_ARG, "bad arguments");
+  lsk::posterior_kernel<<<T, 256, 0, (cudaStream_t)stream>>>(alpha, beta, ctx->N, t_from, 0, p_out);
+  CUDA_TRY(cudaGetLastError());
   return LS_OK;
 }
 

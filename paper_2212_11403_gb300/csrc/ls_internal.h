@@ -22,6 +22,21 @@ struct PropKernelInfo {
 
 void ls_register_prop_kernels(std::vector<PropKernelInfo>& out);
 
+// shared by the translation units: set the thread's error message and return code; device
+// allocation with LS_ERR_OOM on failure
+int ls_fail(int code, const char* fmt, ...);
+int ls_dev_alloc(void** p, size_t bytes);
+
+namespace lsk {
+struct SparseParams;
+}
+cudaError_t ls_launch_sparse(int dir, const lsk::SparseParams& p, cudaStream_t s);
+cudaError_t ls_launch_lookahead(const int32_t* idx, int N, int Wn, int K, int span, int32_t* U, cudaStream_t s);
+cudaError_t ls_launch_sparse_hdist(const float* P, const int32_t* idx, int N, int K, int Wn, const int* win_of_slot,
+                                   int D, float* h, cudaStream_t s);
+cudaError_t ls_launch_dense_rows_hdist(const float* prod, int nf, int N, const int* tlist, int D, float* h,
+                                       cudaStream_t s);
+
 struct ls_ctx {
   int device = 0;
   int N = 0, L = 0, row_words = 0;

@@ -44,8 +44,10 @@ struct PropParams {
   int rw2;
   int N, L;
   int dir;                // 0 forward, 1 backward (selects the instantiation on the host)
-  int t_begin, t_count;   // targets handled by this launch (absolute ids)
-  int tab_t0;             // table row r <-> target tab_t0 + r
+  int t_begin, t_count;   // targets handled by this launch (absolute ids, or positions in tlist)
+  int tab_t0;             // table row r <-> target tab_t0 + r (with tlist: list position tab_t0 + r)
+  const int* tlist;       // optional target list (one target per CTA variants): CTA b takes target
+                          // tlist[t_begin + b]
   int l_first;            // locus of step 0
   int n_steps;            // steps (loci) processed
   int init;               // 1: step 0 is the initial locus (fwd 0 / bwd L-1), no prior state
@@ -246,7 +248,10 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   const int lane = tid & 31, warp = tid >> 5;
   const int tl = lane % TPW;
   const int sl = lane / TPW;
-  const int o = p.t_begin + blockIdx.x * TPW;  // first target of this CTA (< N)
+  const int cta_t = p.t_begin + blockIdx.x * TPW;      // first target (or list position) of the CTA
+  const int o = p.tlist ? p.tlist[cta_t] : cta_t;       // first target of this CTA (< N)
+  const int row0 = cta_t - p.tab_t0;                   // table row of target o
+  const int t_end = p.t_begin + p.t_count;
   int start, len;
   slice_of(warp * SPW + sl, S, N, start, len);
   const int b0 = start + o;                     // first bit of this lane's slice in a doubled row
@@ -269,14 +274,13 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       int st, ln_s;
       slice_of(sg, S, N, st, ln_s);
       const int gs = 32 * c + s;
-      const int tgt = o + t_s;
       float* sp = stg + src * C::STG_STRIDE + s;
       const bool diag = sg == 0 && gs == t_s;
-      const bool ok = gs < ln_s && tgt < p.t_begin + p.t_count;
+      const bool ok = gs < ln_s && cta_t + t_s < t_end;
       int d = st + gs + o;
       d = d >= N ? d - N : d;
       d = d >= N ? d - N : d;
-      float* g = gbase + (size_t)(tgt - p.tab_t0) * N;
+      float* g = gbase + (size_t)(row0 + t_s) * N;
       if (to_global) {
         if (ok) {
           const float v = diag ? 0.0f : *sp;
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     if (ST == 2) s_hlut[0][tid] = ((e >> k) & 1) ? 0.0f : (p.eta_vec ? p.eta_vec[p.l_first] : p.eta);
   }
   if (tid < TPW) {
-    lgs[tid] = (o + tid < p.t_begin + p.t_count && p.logs && !p.init) ? p.logs[o + tid - p.tab_t0] : 0.0;
+    lgs[tid] = (cta_t + tid < t_end && p.logs && !p.init) ? p.logs[row0 + tid] : 0.0;
     sts[tid] = 0u;
   }
   __syncthreads();
@@ -657,8 +661,8 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       if (ST) store_tile(p.wstate, 0, 0.f, 0.f, true);
     }
   }
-  if (tid < TPW && o + tid < p.t_begin + p.t_count) {
-    const int row = o + tid - p.tab_t0;
+  if (tid < TPW && cta_t + tid < t_end) {
+    const int row = row0 + tid;
     const uint32_t stb = sts[tid] | (*flag ? 4u : 0u);  // 4 = LS_STATUS_TIMEOUT
     if (p.logs) p.logs[row] = lgs[tid];
     if (ST && p.stat_out) p.stat_out[row] = (double)wsum_prev / (double)sig_prev;

@@ -1,0 +1,345 @@
+// ls_propose.cuh -- donor proposal for the sparse recursions: window match-count features, a
+// first-stage pre-filter, the MLP scorer (BF16 tensor-core MMA, FP32 accumulation) and top-K.
+//
+// Windows hold 256 consecutive loci.  For haplotypes i, j and window w the feature is the match
+// count m_ij^w = n_w - popcount(h_i^w XOR h_j^w) (n_w = loci in the window).  Stage 1 keeps, for
+// target i and window w, the C donors with the smallest mismatch sum over windows w-1..w+1 (ties
+// to the lower donor id, never i itself).  Stage 2 scores each candidate with the MLP on the
+// match fractions m^{w+d}/n_{w+d}, d = -3..3 (windows clamped to the range), and keeps the K best
+// (ties to the lower id).  Sets are written in ascending donor order.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace lsk {
+
+constexpr int kPropWS = 256;       // loci per window
+constexpr int kFeat = 16;          // feature slots per candidate (7 used, zero padded to one MMA k-step)
+constexpr int kFeatUsed = 7;
+constexpr int kHidden = 256;
+constexpr int kMlpRows = 128;      // candidates per MLP tile
+constexpr int kHS = kHidden + 8;   // padded row stride (bf16) of the hidden tiles in shared memory
+
+// Haplotype-major window bits: hw[(w*N + i)*8 + k] bit b = allele of haplotype i at locus
+// w*256 + 32k + b (0 beyond L).  grid (ceil(N/32), 8, Wn), one warp: a 32 x 32 bit transpose by
+// ballots.
+__global__ void hapmajor_kernel(const uint32_t* __restrict__ bits, int row_words, int N, int L,
+                                uint32_t* __restrict__ hw) {
+  const int g = blockIdx.x, k = blockIdx.y, w = blockIdx.z, lane = threadIdx.x;
+  const int l = w * kPropWS + 32 * k + lane;
+  const uint32_t word = l < L ? bits[(size_t)l * row_words + g] : 0u;
+  uint32_t mine = 0u;
+#pragma unroll
+  for (int h = 0; h < 32; ++h) {
+    const uint32_t b = __ballot_sync(0xffffffffu, (word >> h) & 1u);
+    if (lane == h) mine = b;
+  }
+  const int i = 32 * g + lane;
+  if (i < N) hw[((size_t)w * N + i) * 8 + k] = mine;
+}
+
+// Mismatch counts of one window, min(popcount, 255) as bytes: M[i*Np + j].  64 x 64 pairs per
+// block of 256 threads; thread t handles row t/4 and 16 consecutive columns (one 16-byte store).
+__global__ void mismatch_kernel(const uint32_t* __restrict__ hw, int N, int Np, uint8_t* __restrict__ M) {
+  __shared__ uint32_t A[64][9], B[64][9];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  for (int e = threadIdx.x; e < 64 * 8; e += 256) {
+    const int r = e >> 3, k = e & 7;
+    A[r][k] = i0 + r < N ? hw[(size_t)(i0 + r) * 8 + k] : 0u;
+    B[r][k] = j0 + r < N ? hw[(size_t)(j0 + r) * 8 + k] : 0u;
+  }
+  __syncthreads();
+  const int r = threadIdx.x >> 2, c0 = (threadIdx.x & 3) * 16;
+  uint32_t a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = A[r][k];
+  uint32_t packed[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m += __popc(a[k] ^ B[c0 + c][k]);
+    packed[c >> 2] |= (uint32_t)min(m, 255) << (8 * (c & 3));
+  }
+  if (i0 + r < N && j0 + c0 < Np)
+    *reinterpret_cast<uint4*>(M + (size_t)(i0 + r) * Np + j0 + c0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+}
+
+// Stage 1 for one window, one block (256 threads) per target i: the C donors with the smallest
+// mismatch sum over the available windows among w-1..w+1 (score <= 765), ties to the lower id,
+// written in ascending id order together with their features (match fractions of windows
+// w-3..w+3, clamped).  Ms[d] = count matrix of window w+d-3 (clamped), nv[d] its locus count.
+struct Stage1Args {
+  const uint8_t* Ms[7];
+  float inv_nv[7];
+  int use[3];  // whether windows w-1, w, w+1 exist
+};
+
+__global__ void stage1_kernel(Stage1Args a, int N, int Np, int C, int32_t* __restrict__ cand,
+                              __nv_bfloat16* __restrict__ feat, float* __restrict__ feat32) {
+  constexpr int NB = 768;
+  __shared__ int hist[NB];
+  __shared__ int wsum[8];
+  __shared__ int thr_s, need_eq_s;
+  const int i = blockIdx.x;
+  const uint8_t* r0 = a.Ms[2] + (size_t)i * Np;
+  const uint8_t* r1 = a.Ms[3] + (size_t)i * Np;
+  const uint8_t* r2 = a.Ms[4] + (size_t)i * Np;
+  auto score = [&](int j) -> int {
+    return (a.use[0] ? (int)r0[j] : 0) + (a.use[1] ? (int)r1[j] : 0) + (a.use[2] ? (int)r2[j] : 0);
+  };
+  for (int b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x)
+    if (j != i) atomicAdd(&hist[score(j)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // threshold: the smallest T with #{score <= T} >= C
+    int acc = 0, T = NB - 1, need = 0;
+    for (int b = 0; b < NB; ++b) {
+      if (acc + hist[b] >= C) {
+        T = b;
+        need = C - acc;
+        break;
+      }
+      acc += hist[b];
+    }
+    thr_s = T;
+    need_eq_s = need;
+  }
+  __syncthreads();
+  const int T = thr_s, need_eq = need_eq_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int base_sel = 0, base_eq = 0;
+  for (int j0 = 0; j0 < N; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    const int sc = (j < N && j != i) ? score(j) : 1 << 30;
+    const bool lt = sc < T, eq = sc == T;
+    // rank of this equal-score donor among equal ones (ascending j)
+    const uint32_t be = __ballot_sync(0xffffffffu, eq);
+    if (lane == 0) wsum[warp] = __popc(be);
+    __syncthreads();
+    int eq_before = base_eq;
+    for (int w2 = 0; w2 < warp; ++w2) eq_before += wsum[w2];
+    eq_before += __popc(be & ((1u << lane) - 1u));
+    int eq_tot = 0;
+    for (int w2 = 0; w2 < 8; ++w2) eq_tot += wsum[w2];
+    __syncthreads();
+    const bool sel = lt || (eq && eq_before < need_eq);
+    const uint32_t bs = __ballot_sync(0xffffffffu, sel);
+    if (lane == 0) wsum[warp] = __popc(bs);
+    __syncthreads();
+    int pos = base_sel;
+    for (int w2 = 0; w2 < warp; ++w2) pos += wsum[w2];
+    pos += __popc(bs & ((1u << lane) - 1u));
+    int sel_tot = 0;
+    for (int w2 = 0; w2 < 8; ++w2) sel_tot += wsum[w2];
+    __syncthreads();
+    if (sel && pos < C) {
+      cand[(size_t)i * C + pos] = j;
+      float f[kFeatUsed];
+#pragma unroll
+      for (int d = 0; d < kFeatUsed; ++d) f[d] = 1.0f - (float)a.Ms[d][(size_t)i * Np + j] * a.inv_nv[d];
+      if (feat) {
+        __nv_bfloat16* fo = feat + ((size_t)i * C + pos) * kFeat;
+#pragma unroll
+        for (int d = 0; d < kFeat; ++d) fo[d] = __float2bfloat16_rn(d < kFeatUsed ? f[d] : 0.0f);
+      }
+      if (feat32) {
+        float* fo = feat32 + ((size_t)i * C + pos) * 8;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) fo[d] = d < kFeatUsed ? f[d] : 0.0f;
+      }
+    }
+    base_sel += sel_tot;
+    base_eq += eq_tot;
+  }
+  // fewer than C donors (C >= N): pad with -1
+  for (int q = base_sel + threadIdx.x; q < C; q += blockDim.x) cand[(size_t)i * C + q] = -1;
+}
+
+// MLP parameters on the device: BF16 transposed weights for the MMA, FP32 biases.
+struct MlpDev {
+  const __nv_bfloat16* w1t;  // [256][16]  w1t[n][k] = W1[k][n]
+  const float* b1;           // [256]
+  const __nv_bfloat16* w2t;  // [256][256] w2t[n][k] = W2[k][n]
+  const float* b2;           // [256]
+  const float* w3;           // [256]
+  float b3;
+};
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// scores[r] = w3 . relu(W2^T relu(W1^T x_r + b1) + b2) + b3 for n rows of BF16 features.
+// Persistent: each CTA stages the weights once and loops over tiles of 128 rows; warp w owns rows
+// 16w..16w+15 of a tile and all 256 hidden units (two halves of 128).
+__global__ void __launch_bounds__(256, 1) mlp_score_kernel(MlpDev m, const __nv_bfloat16* __restrict__ X, long long n,
+                                                            float* __restrict__ scores) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem);             // [256][kHS]
+  __nv_bfloat16* H1 = W2s + kHidden * kHS;                                 // [128][kHS]
+  __nv_bfloat16* W1s = H1 + kMlpRows * kHS;                                // [256][24]
+  __nv_bfloat16* Xs = W1s + kHidden * 24;                                  // [128][24]
+  float* bias = reinterpret_cast<float*>(Xs + kMlpRows * 24);              // b1[256], b2[256], w3[256]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tg = lane & 3;
+  for (int e = tid; e < kHidden * kHidden; e += 256) W2s[(e >> 8) * kHS + (e & 255)] = m.w2t[e];
+  for (int e = tid; e < kHidden * kFeat; e += 256) W1s[(e >> 4) * 24 + (e & 15)] = m.w1t[e];
+  for (int e = tid; e < kHidden; e += 256) {
+    bias[e] = m.b1[e];
+    bias[256 + e] = m.b2[e];
+    bias[512 + e] = m.w3[e];
+  }
+  __syncthreads();
+  const long long ntile = (n + kMlpRows - 1) / kMlpRows;
+  for (long long t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const long long r0 = t * kMlpRows;
+    for (int e = tid; e < kMlpRows * kFeat; e += 256) {
+      const int r = e >> 4, k = e & 15;
+      Xs[r * 24 + k] = r0 + r < n ? X[(r0 + r) * kFeat + k] : __float2bfloat16_rn(0.0f);
+    }
+    __syncthreads();
+    const int rw = 16 * warp;  // first row of this warp
+    // layer 1: one k-step of 16
+    uint32_t ax[4];
+    ax[0] = *reinterpret_cast<const uint32_t*>(Xs + (rw + g) * 24 + 2 * tg);
+    ax[1] = *reinterpret_cast<const uint32_t*>(Xs + (rw + g + 8) * 24 + 2 * tg);
+    ax[2] = *reinterpret_cast<const uint32_t*>(Xs + (rw + g) * 24 + 2 * tg + 8);
+    ax[3] = *reinterpret_cast<const uint32_t*>(Xs + (rw + g + 8) * 24 + 2 * tg + 8);
+#pragma unroll 4
+    for (int nt = 0; nt < 32; ++nt) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      const int nc = 8 * nt + g;  // B column of this thread
+      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(W1s + nc * 24 + 2 * tg);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(W1s + nc * 24 + 2 * tg + 8);
+      mma_bf16(d, ax, b0, b1);
+      const int c = 8 * nt + 2 * tg;
+      const float h00 = fmaxf(d[0] + bias[c], 0.f), h01 = fmaxf(d[1] + bias[c + 1], 0.f);
+      const float h10 = fmaxf(d[2] + bias[c], 0.f), h11 = fmaxf(d[3] + bias[c + 1], 0.f);
+      *reinterpret_cast<uint32_t*>(H1 + (rw + g) * kHS + c) = pack_bf16(h00, h01);
+      *reinterpret_cast<uint32_t*>(H1 + (rw + g + 8) * kHS + c) = pack_bf16(h10, h11);
+    }
+    __syncwarp();
+    // layers 2 and 3: two halves of 128 hidden units, 16 k-steps each
+    float s_lo = 0.f, s_hi = 0.f;  // rows rw+g and rw+g+8
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      float acc[16][4];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+#pragma unroll 2
+      for (int ks = 0; ks < 16; ++ks) {
+        const int k0 = 16 * ks;
+        uint32_t ah[4];
+        ah[0] = *reinterpret_cast<const uint32_t*>(H1 + (rw + g) * kHS + k0 + 2 * tg);
+        ah[1] = *reinterpret_cast<const uint32_t*>(H1 + (rw + g + 8) * kHS + k0 + 2 * tg);
+        ah[2] = *reinterpret_cast<const uint32_t*>(H1 + (rw + g) * kHS + k0 + 2 * tg + 8);
+        ah[3] = *reinterpret_cast<const uint32_t*>(H1 + (rw + g + 8) * kHS + k0 + 2 * tg + 8);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int nc = 128 * half + 8 * q + g;
+          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(W2s + nc * kHS + k0 + 2 * tg);
+          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(W2s + nc * kHS + k0 + 2 * tg + 8);
+          mma_bf16(acc[q], ah, b0, b1);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int c = 128 * half + 8 * q + 2 * tg;
+        s_lo += fmaxf(acc[q][0] + bias[256 + c], 0.f) * bias[512 + c] + fmaxf(acc[q][1] + bias[257 + c], 0.f) * bias[513 + c];
+        s_hi += fmaxf(acc[q][2] + bias[256 + c], 0.f) * bias[512 + c] + fmaxf(acc[q][3] + bias[257 + c], 0.f) * bias[513 + c];
+      }
+    }
+    s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 1);
+    s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 2);
+    s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 1);
+    s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 2);
+    if (tg == 0) {
+      if (r0 + rw + g < n) scores[r0 + rw + g] = s_lo + m.b3;
+      if (r0 + rw + g + 8 < n) scores[r0 + rw + g + 8] = s_hi + m.b3;
+    }
+    __syncthreads();  // Xs and H1 are rewritten by the next tile
+  }
+}
+
+__host__ __device__ inline int mlp_smem_bytes() {
+  return (kHidden * kHS + kMlpRows * kHS + kHidden * 24 + kMlpRows * 24) * 2 + 3 * kHidden * 4;
+}
+
+// Stage 2, one block (256 threads) per target: the K best of C candidates by score (higher first,
+// ties to the lower id; -1 entries last), written to idx[(i*Wn + w)*K ...] in ascending id order.
+// Bitonic sorts in shared memory over P = next power of two >= C (<= 2048).
+__global__ void topk_kernel(const int32_t* __restrict__ cand, const float* __restrict__ scores, int C, int K, int P,
+                            int Wn, int w, int32_t* __restrict__ idx) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* key = reinterpret_cast<float*>(smem);
+  int* val = reinterpret_cast<int*>(key + P);
+  const int i = blockIdx.x;
+  for (int q = threadIdx.x; q < P; q += blockDim.x) {
+    const int j = q < C ? cand[(size_t)i * C + q] : -1;
+    val[q] = j;
+    key[q] = (j >= 0 && scores) ? scores[(size_t)i * C + q] : -3.0e38f;
+  }
+  __syncthreads();
+  // order: higher key first, then lower id (ids >= 0 before -1)
+  auto before = [&](int a, int b) -> bool {
+    if (key[a] != key[b]) return key[a] > key[b];
+    const unsigned ua = (unsigned)val[a], ub = (unsigned)val[b];
+    return ua < ub;
+  };
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        const int o = q ^ stride;
+        if (o > q) {
+          const bool up = (q & size) == 0;
+          if (before(o, q) == up) {
+            const float tk = key[q];
+            key[q] = key[o];
+            key[o] = tk;
+            const int tv = val[q];
+            val[q] = val[o];
+            val[o] = tv;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // the first K by ascending id: sort ids of positions < K (others become +inf)
+  for (int q = threadIdx.x; q < P; q += blockDim.x) {
+    const int j = q < K ? val[q] : -1;
+    val[q] = j;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        const int o = q ^ stride;
+        if (o > q) {
+          const bool up = (q & size) == 0;
+          const unsigned a = (unsigned)val[q], b = (unsigned)val[o];
+          if ((a > b) == up) {
+            val[q] = (int)b;
+            val[o] = (int)a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int q = threadIdx.x; q < K; q += blockDim.x) idx[((size_t)i * Wn + w) * K + q] = val[q];
+}
+
+}  // namespace lsk

@@ -1,0 +1,46 @@
+// ls_sparse.cu -- instantiations and launchers of the sparse (proposed-set) recursions.
+#include "ls_internal.h"
+#include "ls_sparse.cuh"
+
+namespace {
+template <int KS>
+cudaError_t launch_ks(int dir, const lsk::SparseParams& p, cudaStream_t s) {
+  const int smem = lsk::sparse_smem_bytes(p.row_words, KS);
+  const void* f = dir == 0 ? (const void*)lsk::ls_sparse_kernel<0, KS> : (const void*)lsk::ls_sparse_kernel<1, KS>;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (p.t_count + lsk::kSparseWarps - 1) / lsk::kSparseWarps;
+  if (dir == 0) lsk::ls_sparse_kernel<0, KS><<<grid, lsk::kSparseWarps * 32, smem, s>>>(p);
+  else lsk::ls_sparse_kernel<1, KS><<<grid, lsk::kSparseWarps * 32, smem, s>>>(p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+// slots per lane: the smallest of 1, 2, 4, 8, 16, 32, 48 with 32 * KS >= K (K <= 1536)
+cudaError_t ls_launch_sparse(int dir, const lsk::SparseParams& p, cudaStream_t s) {
+  if (p.K <= 32) return launch_ks<1>(dir, p, s);
+  if (p.K <= 64) return launch_ks<2>(dir, p, s);
+  if (p.K <= 128) return launch_ks<4>(dir, p, s);
+  if (p.K <= 256) return launch_ks<8>(dir, p, s);
+  if (p.K <= 512) return launch_ks<16>(dir, p, s);
+  if (p.K <= 1024) return launch_ks<32>(dir, p, s);
+  return launch_ks<48>(dir, p, s);
+}
+
+cudaError_t ls_launch_lookahead(const int32_t* idx, int N, int Wn, int K, int span, int32_t* U, cudaStream_t s) {
+  const long long n = (long long)N * Wn;
+  lsk::lookahead_sets_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(idx, N, Wn, K, span, U);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_launch_sparse_hdist(const float* P, const int32_t* idx, int N, int K, int Wn, const int* win_of_slot,
+                                   int D, float* h, cudaStream_t s) {
+  lsk::sparse_hdist_kernel<<<dim3(N, D), 256, 0, s>>>(P, idx, N, K, Wn, win_of_slot, h);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_launch_dense_rows_hdist(const float* prod, int nf, int N, const int* tlist, int D, float* h,
+                                       cudaStream_t s) {
+  lsk::dense_rows_hdist_kernel<<<dim3(nf, D), 256, 0, s>>>(prod, nf, N, tlist, h);
+  return cudaGetLastError();
+}

@@ -1,0 +1,298 @@
+// ls_sparse.cuh -- the LS recursions restricted to proposed donor sets.
+//
+// For target i and window w (WS consecutive loci) the copying state ranges over a set S_i^w of at
+// most K donors (ascending ids, -1 padding at the end).  The prior keeps its dense value
+// pi = 1/(N-1): recombination mass that would go to donors outside the set is dropped, so donors
+// in the set follow exactly the dense recursions (Eq. fwd1 / Eq. bck1) up to a common factor per
+// target and locus.  A transition from locus l (window w) to l+1 (window w') continues only for
+// donors in both sets:
+//   forward:  alpha'_k = theta_k ((1-rho) a_k [k in S] + rho pi),  a = alpha / sum_{S} alpha,
+//   backward: beta_j   = (1-rho) [j in S'] t_j / S + rho,  t = theta beta,  S = pi sum_{k in S'} t_k,
+// so the backward is the adjoint of the forward and p ~ alpha beta over S_i^w is the posterior of
+// the restricted chain.  The normalised forward mass on donors that leave the set at a window
+// change is the in-set check: its maximum per target is reported ("lost"), and targets above a
+// tolerance are recomputed densely by the caller.
+//
+// One warp per target, slot s of lane q <-> set index 32 s + q (coalesced set loads and stores);
+// eight targets per CTA share the packed locus rows, staged eight rows at a time in shared memory.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsk {
+
+constexpr int kSparseWarps = 8;  // targets per CTA
+constexpr int kSparseRows = 8;   // rows staged per block
+
+struct SparseParams {
+  const uint32_t* bits;  // packed rows [L][row_words]: haplotype j = bit j%32 of word j/32
+  int row_words;
+  int N, L;
+  int K;                 // set entries per target and window
+  int WS;                // loci per window
+  int Wn;                // windows, ceil(L / WS)
+  const int32_t* idx;    // [N][Wn][K] donor ids, ascending, -1 padding at the end
+  const float* omr;      // [L-1] 1 - rho
+  const float* rho;      // [L-1] rho
+  const float* thm;      // [L] 1 - mu
+  const float* thx;      // [L] mu
+  int t_begin, t_count;
+  int n_store;
+  int store_loci[64];    // processing order
+  int store_slot[64];
+  float* store;          // [slots][N][K]: forward writes alpha, backward overwrites it with p
+  double* logs;          // [N] forward: log-likelihood of the restricted chain (may be null)
+  float* lost;           // [N] forward: max normalised mass on leaving donors (may be null)
+  uint32_t* status;      // [N] status bits (may be null)
+};
+
+__host__ __device__ inline int sparse_smem_bytes(int row_words, int ks) {
+  return kSparseRows * row_words * 4 + 2 * kSparseWarps * 32 * ks * 4;
+}
+
+#ifndef LS_SPARSE_PARAMS_ONLY  // the kernels live in ls_sparse.cu only
+
+template <int DIR, int KS>
+__global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const SparseParams p) {
+  constexpr float eps = 2.220446049250313e-16f;
+  constexpr int INF_ID = 0x7fffffff;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int rwd = p.row_words;
+  uint32_t* rows = reinterpret_cast<uint32_t*>(smem);
+  int* sid_all = reinterpret_cast<int*>(smem + kSparseRows * rwd * 4);
+  float* sval_all = reinterpret_cast<float*>(sid_all + kSparseWarps * 32 * KS);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i_raw = p.t_begin + blockIdx.x * kSparseWarps + warp;
+  const bool active = i_raw < p.t_begin + p.t_count;
+  const int i = active ? i_raw : p.t_begin;  // idle warps shadow a valid target and write nothing
+  int* sid = sid_all + warp * 32 * KS;
+  float* sval = sval_all + warp * 32 * KS;
+  const int K = p.K, L = p.L;
+  const float pi = 1.0f / (float)(p.N - 1);  // dense uniform prior
+
+  int id[KS];
+  float x[KS];
+  int cur_w = -1;
+  auto warp_sum = [&](float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+  };
+  auto set_entry = [&](int w, int s) -> int {
+    const int q = 32 * s + lane;
+    return q < K ? p.idx[((size_t)i * p.Wn + w) * K + q] : -1;
+  };
+  // enter window w: map the values of the old set onto the new one (0 for new donors); returns the
+  // mapped total
+  auto enter = [&](int w, bool map) -> float {
+    if (map) {
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        sid[32 * s + lane] = id[s] >= 0 ? id[s] : INF_ID;
+        sval[32 * s + lane] = x[s];
+      }
+      __syncwarp();
+    }
+    float mapped = 0.0f;
+#pragma unroll
+    for (int s = 0; s < KS; ++s) {
+      id[s] = set_entry(w, s);
+      float v = 0.0f;
+      if (map && id[s] >= 0) {
+        int lo = 0, hi = 32 * KS;  // first position with sid >= id
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (sid[mid] < id[s]) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < 32 * KS && sid[lo] == id[s]) v = sval[lo];
+      }
+      x[s] = v;
+      mapped += v;
+    }
+    if (map) __syncwarp();
+    cur_w = w;
+    return warp_sum(mapped);
+  };
+
+  double logacc = 0.0;
+  uint32_t stb = 0u;
+  float lost_max = 0.0f;
+  float sum_prev = 1.0f;  // forward: sum alpha; backward: sum t over the set
+  int store_next = 0;
+  const int nblk = (L + kSparseRows - 1) / kSparseRows;
+  for (int b = 0; b < nblk; ++b) {
+    // loci of this block in processing order: forward ascending, backward descending
+    const int l0 = DIR == 0 ? b * kSparseRows : L - 1 - b * kSparseRows;
+    const int nrows = min(kSparseRows, L - b * kSparseRows);
+    const int base = DIR == 0 ? l0 : l0 - nrows + 1;  // lowest locus of the block
+    __syncthreads();
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(p.bits + (size_t)base * rwd);
+      uint4* dst = reinterpret_cast<uint4*>(rows);
+      const int n16 = nrows * rwd / 4;
+      for (int e = threadIdx.x; e < n16; e += blockDim.x) dst[e] = src[e];
+    }
+    __syncthreads();
+    for (int k = 0; k < nrows; ++k) {
+      const int l = DIR == 0 ? l0 + k : l0 - k;
+      const uint32_t* row = rows + (l - base) * rwd;
+      const int w = l / p.WS;
+      const uint32_t tb = (row[i >> 5] >> (i & 31)) & 1u;
+      const float tm = p.thm[l], tx = p.thx[l];
+      float c, r;
+      if (cur_w < 0) {  // initial locus: alpha = theta pi ; t = theta (beta = 1)
+        enter(w, false);
+        c = 0.0f;
+        r = DIR == 0 ? pi : 1.0f;
+      } else {
+        const int m = DIR == 0 ? l - 1 : l;  // interval of this transition
+        if (w != cur_w) {
+          const float mapped = enter(w, true);
+          if (DIR == 0 && sum_prev > 0.0f) lost_max = fmaxf(lost_max, 1.0f - mapped / sum_prev);
+        }
+        if (DIR == 0) {
+          c = p.omr[m] / sum_prev;
+          r = p.rho[m] * pi;
+        } else {
+          // S = pi sum_{k in S'} t_k over the set of locus l+1 (the transition's target set)
+          c = p.omr[m] / (pi * sum_prev);
+          r = p.rho[m];
+        }
+      }
+      const bool is_store = store_next < p.n_store && p.store_loci[store_next] == l;
+      float* srow = is_store ? p.store + ((size_t)p.store_slot[store_next] * p.N + i) * K : nullptr;
+      float s = 0.0f;
+      float zb = 0.0f;  // backward store: sum alpha beta
+      float prod[KS];
+#pragma unroll
+      for (int q = 0; q < KS; ++q) {
+        const int j = id[q];
+        float th = 0.0f;
+        if (j >= 0) th = (((row[j >> 5] >> (j & 31)) & 1u) == tb) ? tm : tx;
+        const float u = j >= 0 ? fmaf(c, x[q], r) : 0.0f;  // alpha (fwd) / beta (bwd) before emission
+        if (DIR == 1 && is_store) {
+          const int sq = 32 * q + lane;
+          prod[q] = (sq < K && j >= 0) ? srow[sq] * u : 0.0f;
+          zb += prod[q];
+        }
+        x[q] = th * u;
+        s += x[q];
+      }
+      s = warp_sum(s);
+      if (is_store) {
+        if (DIR == 0) {
+#pragma unroll
+          for (int q = 0; q < KS; ++q) {
+            const int sq = 32 * q + lane;
+            if (active && sq < K) srow[sq] = x[q];
+          }
+        } else {
+          zb = warp_sum(zb);
+          const float inv = zb > 0.0f ? 1.0f / zb : 0.0f;
+#pragma unroll
+          for (int q = 0; q < KS; ++q) {
+            const int sq = 32 * q + lane;
+            if (active && sq < K) srow[sq] = id[q] < 0 ? 0.0f : (zb > 0.0f ? prod[q] * inv : eps);
+          }
+        }
+        ++store_next;
+      }
+      if (s < 1.17549435e-38f) stb |= 1u;      // LS_STATUS_UNDERFLOW
+      if (!(s <= 3.40282347e+38f)) stb |= 2u;  // LS_STATUS_OVERFLOW (infinite or NaN)
+      if (DIR == 0) logacc += (double)logf(s);
+      sum_prev = s;
+    }
+  }
+  if (active && lane == 0) {
+    if (DIR == 0 && p.logs) p.logs[i] = logacc;
+    if (DIR == 0 && p.lost) p.lost[i] = lost_max;
+    if (p.status && stb) atomicOr(p.status + i, stb);
+  }
+}
+
+// Half distances -log(max(p, eps))/2 of the sparse posteriors, scattered into dense [D][N][N]
+// rows that hold NaN wherever a donor was not in the set.  grid (N, D), 256 threads.
+__global__ void sparse_hdist_kernel(const float* __restrict__ P, const int32_t* __restrict__ idx, int N, int K, int Wn,
+                                    const int* __restrict__ win_of_slot, float* __restrict__ h) {
+  constexpr float eps = 2.220446049250313e-16f;
+  const int i = blockIdx.x, k = blockIdx.y;
+  const int w = win_of_slot[k];
+  const int32_t* ids = idx + ((size_t)i * Wn + w) * K;
+  const float* pr = P + ((size_t)k * N + i) * K;
+  float* hr = h + ((size_t)k * N + i) * N;
+  for (int q = threadIdx.x; q < K; q += blockDim.x) {
+    const int j = ids[q];
+    if (j >= 0 && j < N && j != i) hr[j] = -0.5f * logf(fmaxf(pr[q], eps));
+  }
+}
+
+// Dense fallback rows: products alpha * beta of nf listed targets ([D][nf][N]) normalised into
+// half distances of rows tlist[r] of h ([D][N][N]).  grid (nf, D), 256 threads.
+__global__ void dense_rows_hdist_kernel(const float* __restrict__ prod, int nf, int N, const int* __restrict__ tlist,
+                                        float* __restrict__ h) {
+  constexpr float eps = 2.220446049250313e-16f;
+  const int r = blockIdx.x, k = blockIdx.y;
+  const int i = tlist[r];
+  const float* a = prod + ((size_t)k * nf + r) * N;
+  float s = 0.0f;
+  for (int j = threadIdx.x; j < N; j += blockDim.x)
+    if (j != i) s += a[j];
+  __shared__ float red[32];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float Z = red[0];
+  const float invZ = Z > 0.0f ? 1.0f / Z : 0.0f;
+  float* o = h + ((size_t)k * N + i) * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const float q = Z > 0.0f ? a[j] * invZ : eps;
+    o[j] = j == i ? 0.0f : -0.5f * logf(fmaxf(q, eps));
+  }
+}
+
+// Widened sets: U^w = S^w u S^{w+1} (span 1) or S^{w-1} u S^w u S^{w+1} (span 2), missing windows
+// empty.  A donor proposed for window w+1 is already carried through window w, so it enters with
+// a window of history; with span 2 a donor proposed for window w also stays through w+1, so the
+// forward mass of donors about to mismatch decays inside the chain instead of being cut at the
+// window change.  One thread per (target, window): a merge of up to three ascending lists with
+// duplicates removed, -1 padding to (span + 1) K entries.
+__global__ void lookahead_sets_kernel(const int32_t* __restrict__ idx, int N, int Wn, int K, int span,
+                                      int32_t* __restrict__ U) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * Wn) return;
+  const int w = (int)(t % Wn);
+  const int32_t* lists[3];
+  int pos[3] = {0, 0, 0};
+  int nl = 0;
+  if (span >= 2 && w > 0) lists[nl++] = idx + (t - 1) * K;
+  lists[nl++] = idx + t * K;
+  if (w + 1 < Wn) lists[nl++] = idx + (t + 1) * K;
+  const int width = (span + 1) * K;
+  int32_t* u = U + t * width;
+  int o = 0, last = -1;
+  while (true) {
+    int best = -1;
+    for (int q = 0; q < nl; ++q) {
+      const int v = pos[q] < K ? lists[q][pos[q]] : -1;
+      if (v >= 0 && (best < 0 || v < best)) best = v;
+    }
+    if (best < 0) break;
+    for (int q = 0; q < nl; ++q)
+      if (pos[q] < K && lists[q][pos[q]] == best) ++pos[q];
+    if (best != last) u[o++] = best;
+    last = best;
+  }
+  while (o < width) u[o++] = -1;
+}
+
+#endif  // LS_SPARSE_PARAMS_ONLY
+
+}  // namespace lsk

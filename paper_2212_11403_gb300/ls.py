@@ -36,6 +36,7 @@ LS_BWD = 1
 LS_NOALLOC_MAX_N = 65536
 LS_CKPT_F32 = 0
 LS_CKPT_F16 = 1
+LS_MLP_PARAMS = 68353
 
 EXPORTED = [
     "ls_version", "ls_last_error", "ls_create", "ls_create_packed", "ls_destroy", "ls_info", "ls_query",
@@ -43,6 +44,8 @@ EXPORTED = [
     "ls_table_reset", "ls_table_info", "ls_table_read", "ls_forward", "ls_backward", "ls_posterior", "ls_distance",
     "ls_checkpoints", "ls_ckpt_info", "ls_ckpt_read", "ls_ckpt_replay", "ls_ckpt_destroy",
     "ls_run_all", "ls_run_all_noalloc", "ls_pac_grad", "ls_set_profiling", "ls_profile_read",
+    "ls_posterior_rows", "ls_mlp_create", "ls_mlp_destroy", "ls_mlp_get", "ls_mlp_set", "ls_mlp_forward",
+    "ls_mlp_grad", "ls_mlp_train", "ls_propose_window", "ls_propose", "ls_sparse_run_all",
 ]
 
 
@@ -87,6 +90,17 @@ def _load():
         "ls_run_all": ([P, P, I, P, P, P, P], I),
         "ls_run_all_noalloc": ([P, P, I, P, P, P, P], I),
         "ls_pac_grad": ([P, I, I, P, I, P, P, P, P], I),
+        "ls_posterior_rows": ([P, P, P, I, I, P, P], I),
+        "ls_mlp_create": ([P, ctypes.c_uint64, P], I),
+        "ls_mlp_destroy": ([P], I),
+        "ls_mlp_get": ([P, P], I),
+        "ls_mlp_set": ([P, P], I),
+        "ls_mlp_forward": ([P, P, ctypes.c_int64, P, P], I),
+        "ls_mlp_grad": ([P, P, P, I, P, P, P], I),
+        "ls_mlp_train": ([P, P, P, ctypes.c_int64, I, I, ctypes.c_float, ctypes.c_uint64, P, P], I),
+        "ls_propose_window": ([P, I, I, P, P, P], I),
+        "ls_propose": ([P, I, I, P, P, P], I),
+        "ls_sparse_run_all": ([P, P, I, I, I, P, I, P, ctypes.c_float, P, P, P, P, P], I),
         "ls_set_profiling": ([P, I], I),
         "ls_profile_read": ([P, P, P], I),
     }
@@ -327,6 +341,90 @@ def ls_pac_grad(ctx, interval_of, K, t_from=0, t_to=None, stream=None):
                                  int(K), ctypes.byref(pac), ctypes.byref(gm), gr.ctypes.data_as(ctypes.c_void_p),
                                  _stream(stream)))
     return rc, pac.value, gm.value, gr
+
+
+def ls_posterior_rows(ctx, alpha, beta, t_from, p_out, stream=None):
+    import torch
+    T = alpha.shape[0]
+    return _check(_lib.ls_posterior_rows(ctx, _dev(alpha, torch.float32, "alpha"), _dev(beta, torch.float32, "beta"),
+                                         int(t_from), int(T), _dev(p_out, torch.float32, "p_out"), _stream(stream)))
+
+
+def ls_mlp_create(params=None, seed=0):
+    out = ctypes.c_void_p()
+    pp = None
+    if params is not None:
+        params, pp = _host(params, np.float32)
+        if params.size != LS_MLP_PARAMS:
+            raise ValueError("need %d parameters" % LS_MLP_PARAMS)
+    _check(_lib.ls_mlp_create(pp, ctypes.c_uint64(seed), ctypes.byref(out)))
+    return out
+
+
+def ls_mlp_destroy(m):
+    return _check(_lib.ls_mlp_destroy(m))
+
+
+def ls_mlp_get(m):
+    out = np.zeros(LS_MLP_PARAMS, dtype=np.float32)
+    _check(_lib.ls_mlp_get(m, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def ls_mlp_set(m, params):
+    params, pp = _host(params, np.float32)
+    return _check(_lib.ls_mlp_set(m, pp))
+
+
+def ls_mlp_forward(m, X, scores, stream=None):
+    import torch
+    return _check(_lib.ls_mlp_forward(m, _dev(X, torch.float32, "X"), ctypes.c_int64(X.shape[0]),
+                                      _dev(scores, torch.float32, "scores"), _stream(stream)))
+
+
+def ls_mlp_grad(m, X, y, stream=None):
+    """(grad [LS_MLP_PARAMS] float32, loss) of the half mean squared error at the current weights."""
+    import torch
+    g = np.zeros(LS_MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_lib.ls_mlp_grad(m, _dev(X, torch.float32, "X"), _dev(y, torch.float32, "y"), int(X.shape[0]),
+                            g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss), _stream(stream)))
+    return g, loss.value
+
+
+def ls_mlp_train(m, X, y, steps, batch, lr, seed=0, stream=None):
+    import torch
+    loss = ctypes.c_double()
+    _check(_lib.ls_mlp_train(m, _dev(X, torch.float32, "X"), _dev(y, torch.float32, "y"), ctypes.c_int64(X.shape[0]),
+                             int(steps), int(batch), ctypes.c_float(lr), ctypes.c_uint64(seed), ctypes.byref(loss),
+                             _stream(stream)))
+    return loss.value
+
+
+def ls_propose_window(ctx, C, w, cand_out, feat_out=None, stream=None):
+    import torch
+    return _check(_lib.ls_propose_window(ctx, int(C), int(w), _dev(cand_out, torch.int32, "cand_out"),
+                                         _dev(feat_out, torch.float32, "feat_out"), _stream(stream)))
+
+
+def ls_propose(ctx, C, K, mlp, idx_out, stream=None):
+    import torch
+    return _check(_lib.ls_propose(ctx, int(C), int(K), mlp, _dev(idx_out, torch.int32, "idx_out"), _stream(stream)))
+
+
+def ls_sparse_run_all(ctx, idx, K, WS, decode_loci, d_out, lost_tol=-1.0, lost_out=None, status_out=None,
+                      lookahead=2, stream=None):
+    """Returns (rc, pac of the restricted chains, number of dense-fallback targets)."""
+    import torch
+    dl = np.ascontiguousarray(decode_loci, dtype=np.int32)
+    pac = ctypes.c_double()
+    nf = ctypes.c_int32()
+    rc = _check(_lib.ls_sparse_run_all(ctx, _dev(idx, torch.int32, "idx"), int(K), int(WS), int(lookahead),
+                                       dl.ctypes.data_as(ctypes.c_void_p), dl.size, _dev(d_out, torch.float32, "d_out"),
+                                       ctypes.c_float(lost_tol), _dev(lost_out, torch.float32, "lost_out"),
+                                       ctypes.byref(pac), _dev(status_out, torch.int32, "status_out"), ctypes.byref(nf),
+                                       _stream(stream)))
+    return rc, pac.value, nf.value
 
 
 def ls_set_profiling(ctx, enable=True):

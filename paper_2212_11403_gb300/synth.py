@@ -89,7 +89,8 @@ def gamma_prior_f32(seed: int, N: int, chunk: int = 1024) -> np.ndarray:
     return out
 
 
-def make_workload(name: str, N: int | None = None, L: int | None = None, seed: int | None = None) -> dict:
+def make_workload(name: str, N: int | None = None, L: int | None = None, seed: int | None = None,
+                  founders: int | None = None) -> dict:
     """Draw the inputs of a workload (optionally shrunk to N x L for tests).
 
     Returns dict(h uint8 [L, N], rho float64 [L-1] or None, gaps float64 [L-1] (Morgans) and
@@ -100,7 +101,8 @@ def make_workload(name: str, N: int | None = None, L: int | None = None, seed: i
     L = int(cfg["L"] if L is None else L)
     seed = 1000 + cfg["num"] if seed is None else seed
     rng = np.random.default_rng(seed)
-    h = mosaic_haplotypes(rng, N, L, min(cfg["founders"], N), cfg["switch"], cfg["flip"])
+    F = min(cfg["founders"] if founders is None else founders, N)
+    h = mosaic_haplotypes(rng, N, L, F, cfg["switch"], cfg["flip"])
     out = dict(name=name, N=N, L=L, h=h, mu=float(cfg["mu"]), loci=decode_loci(L, min(cfg["D"], L)), seed=seed)
     if cfg["rho"] == "uniform":
         out["rho"] = rng.uniform(cfg["rho_lo"], cfg["rho_hi"], size=L - 1)

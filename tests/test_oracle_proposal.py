@@ -1,0 +1,114 @@
+"""Pins of the proposal oracle (oracle/proposal.py): brute force on tiny inputs and finite
+differences of the network loss."""
+import numpy as np
+
+from oracle import proposal as op
+
+
+def test_mismatch_counts_brute_force():
+    rng = np.random.default_rng(1)
+    L, N = 600, 9
+    h = (rng.random((L, N)) < 0.3).astype(np.uint8)
+    for w in range(op.windows(L)):
+        M = op.mismatch_counts(h, w)
+        lo, hi = 256 * w, min(256 * (w + 1), L)
+        for i in range(N):
+            for j in range(N):
+                assert M[i, j] == min(sum(int(h[l, i] != h[l, j]) for l in range(lo, hi)), 255)
+
+
+def test_mismatch_counts_saturate_at_255():
+    h = np.zeros((256, 2), dtype=np.uint8)
+    h[:, 1] = 1
+    assert op.mismatch_counts(h, 0)[0, 1] == 255
+
+
+def test_stage1_selection_by_brute_force():
+    rng = np.random.default_rng(2)
+    L, N, C = 900, 12, 5
+    h = (rng.random((L, N)) < 0.4).astype(np.uint8)
+    Wn = op.windows(L)
+    for w in range(Wn):
+        cand, feat = op.stage1(h, w, C)
+        for i in range(N):
+            sc = {}
+            for j in range(N):
+                if j == i:
+                    continue
+                s = 0
+                for v in (w - 1, w, w + 1):
+                    if 0 <= v < Wn:
+                        lo, hi = 256 * v, min(256 * (v + 1), L)
+                        s += min(int(np.sum(h[lo:hi, i] != h[lo:hi, j])), 255)
+                sc[j] = s
+            best = sorted(sorted(sc, key=lambda j: (sc[j], j))[:C])
+            assert list(cand[i]) == best
+            # features: match fractions of windows w-3..w+3 (clamped), then 0
+            j = best[0]
+            for d in range(7):
+                v = min(max(w + d - 3, 0), Wn - 1)
+                lo, hi = 256 * v, min(256 * (v + 1), L)
+                assert abs(feat[i, 0, d] - (1 - np.sum(h[lo:hi, i] != h[lo:hi, j]) / (hi - lo))) < 1e-15
+            assert feat[i, 0, 7] == 0.0
+
+
+def test_stage1_pads_when_fewer_donors_than_c():
+    h = (np.random.default_rng(3).random((300, 4)) < 0.5).astype(np.uint8)
+    cand, _ = op.stage1(h, 0, 6)
+    assert np.all(cand[:, 3:] == -1) and np.all(cand[:, :3] >= 0)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(4)
+    p = rng.normal(0, 0.2, op.N_PARAMS)
+    X = rng.random((40, 8))
+    X[:, 7] = 0.0
+    y = rng.random(40)
+    loss, g = op.mlp_loss_grad(p, X, y)
+    assert abs(loss - 0.5 * np.mean((op.mlp_forward(p, X) - y) ** 2)) < 1e-12
+    h = 1e-6
+    for k in list(rng.choice(op.N_PARAMS, 40, replace=False)) + [op.P_B3, op.P_W1, op.P_B1 + 3, op.P_W3 + 7]:
+        e = np.zeros(op.N_PARAMS)
+        e[k] = h
+        fd = (op.mlp_loss_grad(p + e, X, y)[0] - op.mlp_loss_grad(p - e, X, y)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
+
+
+def test_bf16_rounding_matches_definition():
+    # nearest-even rounding to 8 significant bits
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 1.0 + 2 ** -9, -2.5, 3.0e-3])
+    r = op.bf16(x)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                      # half an ulp (2^-7): tie to even
+    assert r[3] == 1.0                      # a quarter ulp rounds down
+    assert r[2] == 1.0 + 2 ** -7            # three quarters of an ulp rounds up
+    assert r[4] == -2.5
+    assert abs(r[5] - 3.0e-3) <= 3.0e-3 * 2 ** -8
+
+
+def test_sparse_oracle_with_full_sets_is_the_dense_oracle():
+    import oracle
+    rng = np.random.default_rng(9)
+    L, N = 40, 6
+    h = (rng.random((L, N)) < 0.4).astype(np.uint8)
+    rho = rng.uniform(0.01, 0.3, L - 1)
+    mu = 0.05
+    ws = 7
+    Wn = (L + ws - 1) // ws
+    sets = np.array([[[j for j in range(N) if j != i]] * Wn for i in range(N)])
+    loci = [0, 13, 39]
+    p = op.sparse_posteriors(h, rho, mu, sets, ws, loci)
+    ref = oracle.run(h, rho, mu, loci, want=("post",))["post"]
+    assert float(np.max(np.abs(p - ref))) < 1e-12
+
+
+def test_lookahead_sets_union():
+    S = np.array([[[1, 3, -1], [2, 3, 5], [0, -1, -1]]])
+    U = op.lookahead_sets(S)
+    assert list(U[0, 0]) == [1, 2, 3, 5, -1, -1]
+    assert list(U[0, 1]) == [0, 2, 3, 5, -1, -1]
+    assert list(U[0, 2]) == [0, -1, -1, -1, -1, -1]
+    V = op.lookahead_sets(S, 2)
+    assert list(V[0, 0]) == [1, 2, 3, 5] + [-1] * 5
+    assert list(V[0, 1]) == [0, 1, 2, 3, 5] + [-1] * 4
+    assert list(V[0, 2]) == [0, 2, 3, 5] + [-1] * 5
