@@ -26,6 +26,8 @@ void ls_register_group6(std::vector<PropKernelInfo>& out);
 void ls_register_group7(std::vector<PropKernelInfo>& out);
 void ls_register_group8(std::vector<PropKernelInfo>& out);
 void ls_register_group9(std::vector<PropKernelInfo>& out);
+void ls_register_group10(std::vector<PropKernelInfo>& out);
+void ls_register_group11(std::vector<PropKernelInfo>& out);
 
 namespace {
 
@@ -61,6 +63,8 @@ std::vector<PropKernelInfo>& registry() {
     ls_register_group7(v);
     ls_register_group8(v);
     ls_register_group9(v);
+    ls_register_group10(v);
+    ls_register_group11(v);
   });
   return v;
 }
@@ -101,8 +105,13 @@ std::vector<Cand> candidates(ls_ctx* c) {
   std::vector<Cand> out;
   const int N = c->N;
   const int pim = c->Pi ? 1 : 0;
+  // the one-warp-per-target kernels are opt-in (LS_WARP=1): measured slower than the CTA kernels
+  // at N = 5000 (no CTA barrier, but the same issue-bound loop with fewer targets sharing a row load)
+  const char* wenv = getenv("LS_WARP");
+  const bool allow_warp = wenv && wenv[0] == '1';
   for (const auto& k : registry()) {
     if (k.st != 0 || k.pim != pim || !k.serves(N)) continue;
+    if (k.warp && !allow_warp) continue;
     const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;
     bool ok = true;
@@ -126,7 +135,8 @@ double cost_of(const Cand& cd, int count, int nsm) {
   const long long per_wave = (long long)nsm * cd.per_sm;
   const long long full = ctas / per_wave, rem = ctas % per_wave;
   // fewer than two warps per scheduler leave the dependent FP32 chain exposed: count it double
-  const double unit = cd.k->w * (cd.k->kq + 3.0) * (cd.per_sm * cd.k->w < 8 ? 2.0 : 1.0);
+  double unit = cd.k->w * (cd.k->kq + 3.0) * (cd.per_sm * cd.k->w < 8 ? 2.0 : 1.0);
+  if (cd.k->warp) unit *= 0.5;  // when enabled, preferred wherever it serves N
   double t = (double)full * cd.per_sm * unit;
   if (rem) t += (double)((rem + nsm - 1) / nsm) * unit;
   return t;

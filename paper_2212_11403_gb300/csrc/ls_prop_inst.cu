@@ -5,6 +5,7 @@
 // given N; the host planner picks the one with the fewest CTA waves x slots per lane.  Variants
 // are spread over translation units (LS_INST_GROUP) so the build compiles them in parallel.
 #include "ls_internal.h"
+#include "ls_warp.cuh"
 
 namespace {
 
@@ -33,7 +34,27 @@ bool serves_prop(int N) {
   return lsk::PropCfg<TPW, W, KQ>::serves(N);
 }
 
+template <int KQ>
+cudaError_t launch_warp(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
+  if (dir == 0) lsk::ls_warp_kernel<0, KQ><<<grid, lsk::kWarpTargets * 32, smem, s>>>(p);
+  else lsk::ls_warp_kernel<1, KQ><<<grid, lsk::kWarpTargets * 32, smem, s>>>(p);
+  return cudaGetLastError();
+}
+template <int KQ>
+int smem_warp(int rw2) {
+  return lsk::WarpCfg<KQ>::smem_bytes(rw2);
+}
+template <int KQ>
+bool serves_warp(int N) {
+  return lsk::WarpCfg<KQ>::serves(N);
+}
+
 }  // namespace
+
+#define LS_REGW(K)                                                                                  \
+  out.push_back(PropKernelInfo{lsk::kWarpTargets, lsk::kWarpTargets, K, 0, 0,                       \
+                               {(const void*)lsk::ls_warp_kernel<0, K>, (const void*)lsk::ls_warp_kernel<1, K>}, \
+                               launch_warp<K>, smem_warp<K>, serves_warp<K>, 1})
 
 #define LS_REGP(T, Wp, K, P)                                                                        \
   out.push_back(PropKernelInfo{T, Wp, K, P, 0,                                                      \
@@ -102,6 +123,19 @@ void ls_register_group7(std::vector<PropKernelInfo>& out) {
   LS_REGP(1, 4, 40, 1);
   LS_REGP(1, 8, 20, 1);
   LS_REGP(8, 4, 16, 1);
+}
+#elif LS_INST_GROUP == 10
+void ls_register_group10(std::vector<PropKernelInfo>& out) {
+  // one warp per target: N <= 5120
+  LS_REGW(40);
+  LS_REGW(32);
+  LS_REGW(24);
+}
+#elif LS_INST_GROUP == 11
+void ls_register_group11(std::vector<PropKernelInfo>& out) {
+  LS_REGW(16);
+  LS_REGW(8);
+  LS_REGW(4);
 }
 #elif LS_INST_GROUP == 8
 void ls_register_group8(std::vector<PropKernelInfo>& out) {

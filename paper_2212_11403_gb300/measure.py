@@ -1,0 +1,168 @@
+"""Timings of the secondary workloads through the library (one JSON line each).
+
+    python -m paper_2212_11403_gb300.measure prior   # N=20000, L=50000, Gamma(2,1) prior matrix, checkpoints
+    python -m paper_2212_11403_gb300.measure grad    # N=L=10000, gradient over 100 rho intervals
+    python -m paper_2212_11403_gb300.measure sparse  # learned sparse path against dense (N=20000) and at N=50000
+
+CUDA events around each call on the current stream, after one warm-up call; inputs resident in
+device memory.  These are measurements of the library only; the accuracy of each path against the
+FP64 oracle is established by the GPU tests.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import ls, proposal, synth
+
+P_FP32 = 2 * 128 * 152 * 2070e6  # FP32 FMA pipe, FLOP/s at the maximum SM clock
+
+
+def timed(fn, reps=1):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+def measure_prior():
+    import torch
+    w = synth.make_workload("ls_n20000_l50000")
+    N, L, loci = w["N"], w["L"], w["loci"]
+    rho = ls.ls_calc_rho(w["gaps"], w["Ne"], 1.0)
+    Pi = torch.from_numpy(synth.gamma_prior_f32(w["pi_seed"], N)).cuda()
+    ctx = ls.ls_create(w["h"])
+    out = []
+    try:
+        ls.ls_set_params(ctx, rho, w["mu"], Pi)
+        d = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+        t = timed(lambda: ls.ls_run_all(ctx, loci, d, want_pac=False))
+        cells = float(N) * N * L
+        # matrix prior: 5 FLOP per cell and direction (one more multiply than the uniform prior)
+        out.append(dict(workload="ls_n20000_l50000", path="dense fwd+bwd+distance, Gamma(2,1) prior matrix", D=len(loci),
+                        seconds=t, cell_updates_per_s=cells / t, flop_per_cell=10,
+                        frac_fp32=10 * cells / t / P_FP32))
+        for dt, name in ((ls.LS_CKPT_F32, "f32"), (ls.LS_CKPT_F16, "f16")):
+            fw = ls.ls_table_create(ctx, ls.LS_FWD, 0, N)
+            box = {}
+
+            def run():
+                ls.ls_table_reset(fw)
+                if "ck" in box:
+                    ls.ls_ckpt_destroy(box.pop("ck"))
+                box["ck"] = ls.ls_checkpoints(ctx, fw, 0, L - 1, dt)
+            t = timed(run)
+            info = ls.ls_ckpt_info(box["ck"])
+            # replay to the middle of the widest gap between snapshots
+            probe = (int(info["loci"][0]) + int(info["loci"][1])) // 2
+            fw2 = ls.ls_table_create(ctx, ls.LS_FWD, 0, N)
+            tr = timed(lambda: ls.ls_ckpt_replay(ctx, box["ck"], fw2, probe))
+            out.append(dict(workload="ls_n20000_l50000", path="forward with %d %s checkpoints" % (info["n"], name),
+                            seconds=t, checkpoint_bytes=info["device_bytes"], replay_to_locus=probe,
+                            replay_seconds=tr, cell_updates_per_s=float(N) * N * L / t))
+            ls.ls_ckpt_destroy(box["ck"])
+            ls.ls_table_destroy(fw)
+            ls.ls_table_destroy(fw2)
+    finally:
+        ls.ls_destroy(ctx)
+    return out
+
+
+def measure_grad():
+    import torch
+    w = synth.make_workload("ls_n10000_l10000")
+    N, L, K = w["N"], w["L"], 100
+    iv = synth.rho_intervals(L, K)
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        tg = timed(lambda: ls.ls_pac_grad(ctx, iv, K))
+        d = torch.empty((1, N, N), dtype=torch.float32, device="cuda")
+        tp = timed(lambda: ls.ls_run_all(ctx, np.array([L // 2], dtype=np.int32), d, want_pac=True))
+    finally:
+        ls.ls_destroy(ctx)
+    cells = float(N) * N * L
+    return [dict(workload="ls_n10000_l10000", path="PAC log-likelihood + gradient (log mu, 100 log rho groups)",
+                 seconds=tg, cell_updates_per_s=cells / tg, plain_fwd_bwd_seconds=tp, ratio_to_plain=tg / tp)]
+
+
+def measure_sparse():
+    import torch
+    out = []
+    C, K = 1024, 512
+    # training on dense posteriors of an N = 5000 instance of the same generator (founders N/25)
+    Nt, Lt = 5000, 20000
+    wt = synth.make_workload("ls_n50000_l20000", N=Nt, L=Lt, seed=5001, founders=Nt // 25)
+    ctx = ls.ls_create(wt["h"])
+    wins = list(range(0, (Lt + 255) // 256, 8))
+    t0 = time.time()
+    try:
+        ls.ls_set_params(ctx, wt["rho"], wt["mu"])
+        X, y = proposal.training_set(ctx, Nt, Lt, C, wins)
+    finally:
+        ls.ls_destroy(ctx)
+    net, loss = proposal.train(X, y, steps=1500, batch=16384, lr=1e-3, seed=3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del X, y
+    for N, judge in ((20000, True), (50000, False)):
+        w = synth.make_workload("ls_n50000_l20000", N=N, seed=6000 + N, founders=N // 25)
+        L = w["L"]
+        loci = synth.decode_loci(L, 4)
+        Wn = (L + 255) // 256
+        ctx = ls.ls_create(w["h"])
+        try:
+            ls.ls_set_params(ctx, w["rho"], w["mu"])
+            rec = dict(workload="ls_n50000_l20000 generator at N=%d" % N, N=N, L=L, D=4, K=K, C=C,
+                       train_seconds=t_train, train_loss=loss)
+            idx = torch.empty((N, Wn, K), dtype=torch.int32, device="cuda")
+            ds = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+            for name, m in (("raw", None), ("mlp", net)):
+                tp = timed(lambda: ls.ls_propose(ctx, C, K, m, idx))
+                ts = timed(lambda: ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds))
+                rec[name] = dict(propose_seconds=tp, sparse_seconds=ts, total_seconds=tp + ts,
+                                 coverage=float(torch.isfinite(ds).float().mean()))
+                if judge:
+                    if "dense_seconds" not in rec:
+                        dd = torch.empty_like(ds)
+                        rec["dense_seconds"] = timed(lambda: ls.ls_run_all(ctx, loci, dd, want_pac=False))
+                    fin = torch.isfinite(ds)
+                    e = (ds - dd).abs()[fin]
+                    smp = e[torch.randperm(e.numel(), device=e.device)[:4000000]]
+                    q = torch.quantile(smp, torch.tensor([0.5, 0.9, 0.99], device=e.device)).tolist()
+                    rec[name].update(dd_q50=q[0], dd_q90=q[1], dd_q99=q[2], dd_max=float(e.max()),
+                                     frac_within_1e3=float((e <= 1e-3).float().mean()),
+                                     speedup=rec["dense_seconds"] / (tp + ts))
+            out.append(rec)
+            del ds
+            if judge:
+                del dd
+        finally:
+            ls.ls_destroy(ctx)
+    ls.ls_mlp_destroy(net)
+    return out
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["prior", "grad", "sparse"])
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    fn = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse)[a.what]
+    for rec in fn():
+        print(json.dumps(rec), flush=True)
+
+
+if __name__ == "__main__":
+    main()
