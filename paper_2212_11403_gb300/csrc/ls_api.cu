@@ -215,6 +215,29 @@ int run_launches(ls_ctx* c, lsk::PropParams p, int t_begin, int t_count, cudaStr
   int rc = plan(c, t_begin, t_count, lp);
   if (rc) return rc;
   if (nlaunch) *nlaunch = (int)lp.size();
+  // A main/tail plan: the tail (few targets, one small CTA per SM, latency-bound) goes first on a
+  // side stream so that its CTAs share SMs with the main waves instead of running after them.
+  const char* ov = getenv("LS_TAIL_OVERLAP");
+  if (lp.size() == 2 && !(ov && ov[0] == '0')) {
+    if (!c->side) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    }
+    CUDA_TRY(cudaEventRecord(c->fork_ev, s));
+    CUDA_TRY(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+    for (int k = 1; k >= 0; --k) {
+      const Launch& L = lp[k];
+      p.t_begin = L.t_begin;
+      p.t_count = L.t_count;
+      cudaError_t e = L.k->launch(p.dir, p, L.grid, L.smem, k == 1 ? c->side : s);
+      if (e != cudaSuccess) return fail(LS_ERR_CUDA, "propagation launch (TPW=%d W=%d KQ=%d): %s", L.k->tpw, L.k->w,
+                                        L.k->kq, cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaEventRecord(c->join_ev, c->side));
+    CUDA_TRY(cudaStreamWaitEvent(s, c->join_ev, 0));
+    return LS_OK;
+  }
   for (const auto& L : lp) {
     p.t_begin = L.t_begin;
     p.t_count = L.t_count;
@@ -267,6 +290,9 @@ void free_ctx(ls_ctx* c) {
   cudaFree(c->dscratch);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 

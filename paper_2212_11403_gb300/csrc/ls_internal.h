@@ -69,6 +69,9 @@ struct ls_ctx {
   bool profile = false;
   bool profiled = false;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // side stream for the tail launch of a main/tail plan (fork/join events on the caller's stream)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int launches[4] = {0, 0, 0, 0};
 };
 

@@ -87,6 +87,14 @@ typedef float2 f2;
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// 16-byte shared load from a 32-bit shared address.  Not volatile and no memory clobber, so the
+// compiler may schedule it like an arithmetic instruction; callers order it after the barrier that
+// publishes the emission table through a data dependency on the address.
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+  float4 v;
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
 __device__ __forceinline__ uint32_t funnel(uint32_t lo, uint32_t hi, uint32_t s) {
   return __funnelshift_r(lo, hi, s);  // (hi:lo) >> s, s in [0, 31]
 }
@@ -239,8 +247,10 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   // indexed by 16 x (4 match bits); static so the table's address folds into the load offset
   __shared__ __align__(256) float s_lut[2][64];
   float* lutf = &s_lut[0][0];
+  const uint32_t lut_base = smem_u32(&s_lut[0][0]);
   // ST 2: eta H for the same 16 x 4 entries (0 on a match, eta on a mismatch)
   __shared__ __align__(256) float s_hlut[ST == 2 ? 2 : 1][ST == 2 ? 64 : 4];
+  const uint32_t hlut_base = smem_u32(&s_hlut[0][0]);
   uint32_t* ring = reinterpret_cast<uint32_t*>(smem + lay.ring_off);
   float* stg = reinterpret_cast<float*>(smem + lay.stg_off);
 
@@ -540,7 +550,12 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
 
     // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
     const uint32_t inv = ((rw[abit >> 5] >> (abit & 31)) & 1u) ? 0u : 0xffffffffu;  // target allele
-    const uint32_t lut_b = p.mu_vec ? (uint32_t)((step & 1) << 8) : 0u;  // byte offset of this step's table
+    // shared address of this step's table (256-byte aligned, so a byte permute can put a nibble
+    // offset in its low byte and the load needs no further address arithmetic)
+    uint32_t lut_b = lut_base + (p.mu_vec ? (uint32_t)((step & 1) << 8) : 0u);
+    // the loads below are plain asm that the compiler may move; deriving their address from a
+    // volatile move here keeps them after the previous locus' barrier (which publishes the table)
+    asm volatile("mov.b32 %0, %0;" : "+r"(lut_b));
     const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
     const f2 CW2 = make_float2(cw, cw), RW2 = make_float2(rws, rws);
     f2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
@@ -560,8 +575,8 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     auto load_th = [&](int kk) -> float4 {
       const int q = kk & 7, m = kk >> 3;
       // PRMT: byte q/2 of the nibble word as the low byte, the table's buffer offset above it
-      const uint32_t off = __byte_perm((q & 1) ? hw[m & 1] : lw[m & 1], lut_b, 0x7650u | (uint32_t)(q >> 1));
-      return *reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(s_lut) + off);
+      const uint32_t a = __byte_perm((q & 1) ? hw[m & 1] : lw[m & 1], lut_b, 0x7650u | (uint32_t)(q >> 1));
+      return lds128(a);
     };
     prep_word(0);
 #pragma unroll
@@ -605,8 +620,8 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
           const f2 v23 = __fmul2_rn(make_float2(t.z, t.w), __ffma2_rn(CW2, wv[kw][1], RW2));
           if (ST == 2) {  // + eta H x (the emission term of the mismatch statistic)
             const int q = k & 7, m = k >> 3;
-            const uint32_t off = __byte_perm((q & 1) ? hw[m & 1] : lw[m & 1], lut_b, 0x7650u | (uint32_t)(q >> 1));
-            const float4 hv = *reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(s_hlut) + off);
+            const uint32_t a = __byte_perm((q & 1) ? hw[m & 1] : lw[m & 1], lut_b, 0x7650u | (uint32_t)(q >> 1));
+            const float4 hv = lds128(a - lut_base + hlut_base);
             wv[kw][0] = __ffma2_rn(make_float2(hv.x, hv.y), x[k][0], v01);
             wv[kw][1] = __ffma2_rn(make_float2(hv.z, hv.w), x[k][1], v23);
           } else {
