@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   // ---- staged transfers between the register tile and global memory (store loci only) ------
   // element (src thread, slot s of chunk c) <-> donor (start_src + 32c + s + o) mod N of target
   // o + tl_src; consecutive threads take consecutive slots, so global accesses are contiguous.
-  auto xfer = [&](int c, float* gbase, int mode, bool to_global) {
+  // to global: w1 = v, m1 *= v, w2 = v (any may be null); from global: gbase into the staging chunk
+  auto xfer = [&](int c, float* gbase, float* w1, float* m1, float* w2, bool to_global) {
     for (int idx = tid; idx < THREADS * 32; idx += THREADS) {
       const int src = idx >> 5, s = idx & 31;
       const int ln = src & 31;
@@ -290,15 +291,16 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       int d = st + gs + o;
       d = d >= N ? d - N : d;
       d = d >= N ? d - N : d;
-      float* g = gbase + (size_t)(row0 + t_s) * N;
+      const size_t ro = (size_t)(row0 + t_s) * N + d;
       if (to_global) {
         if (ok) {
           const float v = diag ? 0.0f : *sp;
-          if (mode == 2) g[d] = diag ? 0.0f : g[d] * v;
-          else g[d] = v;
+          if (w1) w1[ro] = v;
+          if (m1) m1[ro] = diag ? 0.0f : m1[ro] * v;
+          if (w2) w2[ro] = v;
         }
       } else {
-        *sp = (ok && !diag) ? g[d] : 0.0f;
+        *sp = (ok && !diag) ? gbase[ro] : 0.0f;
       }
     }
   };
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   auto load_tile = [&](f2 (&v)[ST ? KQ : 1][2], f2 (&u)[KQ][2], bool into_w, const float* src) {
 #pragma unroll
     for (int c = 0; c < C::NCHUNK; ++c) {
-      xfer(c, const_cast<float*>(src), 0, false);
+      xfer(c, const_cast<float*>(src), nullptr, nullptr, nullptr, false);
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -386,7 +388,8 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   }
 
   // store the tile (mode 0: x; 1: c x + r; 2: multiply the destination by c x + r)
-  auto store_tile = [&](float* gbase, int mode, float c, float r, bool from_w = false) {
+  // stage (affine ? c x + r : x) chunk by chunk and write it to w1 / multiply m1 by it / write w2
+  auto store_tile = [&](float* w1, float* m1, float* w2, bool affine, float c, float r, bool from_w = false) {
     const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
 #pragma unroll
     for (int cc = 0; cc < C::NCHUNK; ++cc) {
@@ -396,13 +399,13 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
         if (k < KQ) {
           const f2 xa = (ST && from_w) ? wv[ST ? k : 0][0] : x[k][0];
           const f2 xb = (ST && from_w) ? wv[ST ? k : 0][1] : x[k][1];
-          const f2 a = mode == 0 ? xa : __ffma2_rn(C2, xa, R2);
-          const f2 b = mode == 0 ? xb : __ffma2_rn(C2, xb, R2);
+          const f2 a = affine ? __ffma2_rn(C2, xa, R2) : xa;
+          const f2 b = affine ? __ffma2_rn(C2, xb, R2) : xb;
           *reinterpret_cast<float4*>(stg + tid * C::STG_STRIDE + 4 * q) = make_float4(a.x, a.y, b.x, b.y);
         }
       }
       __syncthreads();
-      xfer(cc, gbase, mode, true);
+      xfer(cc, nullptr, w1, m1, w2, true);
       __syncthreads();
     }
   };
@@ -534,8 +537,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     const bool is_store = l == next_store_l;
     const bool save_here = p.save_state && step == p.n_steps - 1;
     if (DIR == 0 && pend_slot >= 0) {  // alpha of the previous locus
-      store_tile(p.store + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f);
-      if (ST && p.wstore) store_tile(p.wstore + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f, true);
+      store_tile(p.store + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f);
+      if (ST && p.wstore)
+        store_tile(p.wstore + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f, true);
       pend_slot = -1;
     }
 
@@ -543,9 +547,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       // beta^l = c t^{l+1} + rho, the pre-emission value; when decoding, alpha^l beta^l
       // overwrites alpha^l in place (normalised by the decode kernel)
       const int slot = is_store ? p.store_slot[store_next] : 0;
-      if (is_store && p.store) store_tile(p.store + (size_t)slot * p.state_rows * N, 1, c, r);
-      if (is_store && p.alpha_dec) store_tile(p.alpha_dec + (size_t)slot * p.state_rows * N, 2, c, r);
-      if (save_here) store_tile(p.state, 1, c, r);
+      const size_t so = (size_t)slot * p.state_rows * N;
+      store_tile((is_store && p.store) ? p.store + so : nullptr, (is_store && p.alpha_dec) ? p.alpha_dec + so : nullptr,
+                 save_here ? p.state : nullptr, true, c, r);
     }
 
     // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
@@ -668,12 +672,13 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
 
   if (DIR == 0) {
     if (pend_slot >= 0) {
-      store_tile(p.store + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f);
-      if (ST && p.wstore) store_tile(p.wstore + (size_t)pend_slot * p.state_rows * N, 0, 0.f, 0.f, true);
+      store_tile(p.store + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f);
+      if (ST && p.wstore)
+        store_tile(p.wstore + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f, true);
     }
     if (pend_save) {
-      store_tile(p.state, 0, 0.f, 0.f);
-      if (ST) store_tile(p.wstate, 0, 0.f, 0.f, true);
+      store_tile(p.state, nullptr, nullptr, false, 0.f, 0.f);
+      if (ST) store_tile(p.wstate, nullptr, nullptr, false, 0.f, 0.f, true);
     }
   }
   if (tid < TPW && cta_t + tid < t_end) {
