@@ -670,16 +670,12 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     sig_prev = sig;
   }
 
-  if (DIR == 0) {
-    if (pend_slot >= 0) {
-      store_tile(p.store + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f);
-      if (ST && p.wstore)
-        store_tile(p.wstore + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f, true);
-    }
-    if (pend_save) {
-      store_tile(p.state, nullptr, nullptr, false, 0.f, 0.f);
-      if (ST) store_tile(p.wstate, nullptr, nullptr, false, 0.f, 0.f, true);
-    }
+  if (DIR == 0 && (pend_slot >= 0 || pend_save)) {  // alpha of the last locus and the state, one pass
+    store_tile(pend_slot >= 0 ? p.store + (size_t)pend_slot * p.state_rows * N : nullptr, nullptr,
+               pend_save ? p.state : nullptr, false, 0.f, 0.f);
+    if (ST)
+      store_tile((pend_slot >= 0 && p.wstore) ? p.wstore + (size_t)pend_slot * p.state_rows * N : nullptr, nullptr,
+                 pend_save ? p.wstate : nullptr, false, 0.f, 0.f, true);
   }
   if (tid < TPW && cta_t + tid < t_end) {
     const int row = row0 + tid;
