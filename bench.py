@@ -178,8 +178,9 @@ def run_reference(args, world, rank):
     vals = [r["value"] for r in samples]
     value = float(np.median(vals))
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
-                ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-                data="synthetic founder mosaics (seeded)", impl="reference",
+                ms_per_step=1e3 * float(N) * N * L / value, ms_per_step_basis="whole workload, extrapolated "
+                "linearly in the number of targets from the timed sample", higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic founder mosaics (seeded)", impl="reference",
                 config={"workload": args.workload, "N": N, "L": L, "D": int(len(w["loci"]))},
                 cpu_baseline=dict(value=value, unit=UNIT, cores=samples[-1]["cores"], kind="oracle",
                                   sample=samples[-1]["sample"]),
