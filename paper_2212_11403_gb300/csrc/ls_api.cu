@@ -28,6 +28,8 @@ void ls_register_group8(std::vector<PropKernelInfo>& out);
 void ls_register_group9(std::vector<PropKernelInfo>& out);
 void ls_register_group10(std::vector<PropKernelInfo>& out);
 void ls_register_group11(std::vector<PropKernelInfo>& out);
+void ls_register_group12(std::vector<PropKernelInfo>& out);
+void ls_register_group13(std::vector<PropKernelInfo>& out);
 
 namespace {
 
@@ -65,6 +67,8 @@ std::vector<PropKernelInfo>& registry() {
     ls_register_group9(v);
     ls_register_group10(v);
     ls_register_group11(v);
+    ls_register_group12(v);
+    ls_register_group13(v);
   });
   return v;
 }

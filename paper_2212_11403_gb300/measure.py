@@ -115,7 +115,7 @@ def measure_sparse():
     torch.cuda.synchronize()
     t_train = time.time() - t0
     del X, y
-    for N, judge in ((20000, True), (50000, False)):
+    for N, judge in ((20000, True), (50000, True)):
         w = synth.make_workload("ls_n50000_l20000", N=N, seed=6000 + N, founders=N // 25)
         L = w["L"]
         loci = synth.decode_loci(L, 4)

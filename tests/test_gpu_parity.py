@@ -354,3 +354,71 @@ def test_run_all_n5000_l20000_sampled_targets(ls):
         dref = oracle.distance_block(ref["post"][:, k, :], targets)
         e = d_err(sub[k], dref)
         assert e <= D_TOL, "locus %d: err %.3g" % (loci[k], e)
+
+
+# ---------------------------------------------------------------- large N (state in shared memory)
+@pytest.mark.parametrize("N", [20481, 30001, 50000, 57000])
+def test_run_all_large_n_sampled(ls, N):
+    """N beyond the register-tile kernels (one target per CTA, state in shared memory): d among 16
+    sampled targets and their log-likelihoods against the oracle."""
+    import torch
+    L = 40
+    w = synth.make_workload("ls_n50000_l20000", N=N, L=L, seed=900 + N % 97, founders=N // 25)
+    loci = np.array([0, 19, L - 1], dtype=np.int32)
+    targets = np.sort(np.random.default_rng(N).choice(N, size=16, replace=False))
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        d = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+        rc, pac = ls.ls_run_all(ctx, loci, d)
+        ti = torch.from_numpy(targets.astype(np.int64)).cuda()
+        sub = d[:, ti][:, :, ti].cpu().numpy()
+        del d
+        fw = ls.ls_table_create(ctx, ls.LS_FWD, 0, N)
+        ls.ls_forward(ctx, fw, L - 1)
+        lf = torch.empty(N, dtype=torch.float64, device="cuda")
+        ls.ls_table_read(fw, logscale=lf)
+        torch.cuda.synchronize()
+        ls.ls_table_destroy(fw)
+        lf = lf.cpu().numpy()
+    finally:
+        ls.ls_destroy(ctx)
+    assert rc == 0
+    assert abs(pac - lf.sum()) <= 1e-9 * abs(pac)
+    ref = oracle.run(w["h"], w["rho"], w["mu"], loci, targets=targets, want=("post", "llf"))
+    assert log_close(lf[targets], ref["llf"], L)[0]
+    for k in range(len(loci)):
+        dref = oracle.distance_block(ref["post"][:, k, :], targets)
+        assert d_err(sub[k], dref) <= D_TOL, (N, k, d_err(sub[k], dref))
+
+
+def test_large_n_fallback_rows_match_dense(ls):
+    """the sparse path's dense fallback (one-target CTAs over a target list) at N = 30000."""
+    import torch
+    N, L, K = 30000, 1000, 32
+    w = synth.make_workload("ls_n50000_l20000", N=N, L=L, seed=77, founders=N // 25)
+    loci = np.array([10, 600, 999], dtype=np.int32)
+    Wn = (L + 255) // 256
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        idx = torch.empty((N, Wn, K), dtype=torch.int32, device="cuda")
+        ls.ls_propose(ctx, K, K, None, idx)
+        ds = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+        lost = torch.empty(N, dtype=torch.float32, device="cuda")
+        ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds, lost_tol=-1.0, lost_out=lost)
+        lh = lost.cpu().numpy()
+        tol = float(np.sort(lh)[-11])  # the (at most) ten targets with the largest lost mass fall back
+        rc, _, nf = ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds, lost_tol=tol)
+        fb = np.flatnonzero(~(lh <= tol))
+        assert nf == fb.size > 0
+        ti = torch.from_numpy(fb.astype(np.int64)).cuda()
+        sub = ds[:, ti][:, :, ti].cpu().numpy()
+        del ds
+        dd = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+        ls.ls_run_all(ctx, loci, dd)
+        ref = dd[:, ti][:, :, ti].cpu().numpy()
+        del dd
+    finally:
+        ls.ls_destroy(ctx)
+    assert d_err(sub, ref.astype(np.float64)) <= 1e-5
