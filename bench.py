@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample size, in seconds of CPU work")
+    ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0: every host core)")
     ap.add_argument("--N", type=int, default=None, help="override N (small cases for profiling; not a bench line)")
     ap.add_argument("--L", type=int, default=None, help="override L (small cases for profiling; not a bench line)")
     ap.add_argument("--D", type=int, default=None, help="override the number of decode loci (profiling cases)")
@@ -142,12 +143,12 @@ def make_inputs(name, N=None, L=None):
     return w
 
 
-def oracle_sample(w, seconds, seed=7):
+def oracle_sample(w, seconds, seed=7, threads=0):
     """Time the FP64 oracle (as it stands) on a bounded sample of targets of the same workload."""
     import oracle
     N, L = w["N"], w["L"]
     rng = np.random.default_rng(seed)
-    threads = os.cpu_count() or 1
+    threads = threads if threads > 0 else (os.cpu_count() or 1)
     t0 = time.perf_counter()
     oracle.run(w["h"], w["rho"], w["mu"], w["loci"], targets=rng.choice(N, size=1, replace=False), want=("llf",),
                nthreads=1)
@@ -172,7 +173,7 @@ def run_reference(args, world, rank):
     per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     samples = []
     for s in range(args.warmup + args.steps):
-        r = oracle_sample(w, per_step, seed=100 + s)
+        r = oracle_sample(w, per_step, seed=100 + s, threads=args.cpu_threads)
         if s >= args.warmup:
             samples.append(r)
     vals = [r["value"] for r in samples]
@@ -292,7 +293,7 @@ def main():
         line["e2e"] = {"value": world * cells / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "s_per_step": te}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds)
+        line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds, threads=args.cpu_threads)
     ls.ls_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
