@@ -277,14 +277,17 @@ int ls_propose(ls_ctx* ctx, int32_t C, int32_t K, const ls_mlp* mlp, int32_t* id
  * -1 padding, never the target itself), posteriors and distances at the D decode loci.  Window w
  * runs on S^w (lookahead 0), S^w u S^{w+1} (1: every proposed donor has a window of history when
  * its own window starts) or S^{w-1} u S^w u S^{w+1} (2: proposed donors also stay a window
- * longer); (lookahead + 1) K <= 1536.  d_out
+ * longer); (lookahead + 1) K <= 1536.  With pool = 1 the donors outside the set are carried as one
+ * aggregate state with their average emission (allele counts of the locus minus the set's
+ * matches), so the normalisers include their mass as in the dense chain; leaving donors' mass
+ * joins it and entering donors start from its average.  d_out
  * device float [D][N][N]: d_ij of Eq. distmat where j is in i's set and i in j's set at that
  * locus' window, NaN elsewhere ("uncovered"), 0 on the diagonal.  Targets whose largest forward
  * mass on donors leaving their set exceeds lost_tol (lost_tol < 0: never) get dense rows
  * (requires N within the dense kernels' range); *n_fallback_out receives their number.
  * lost_out device float [N] (may be NULL) receives that mass per target; pac_out the
  * log-likelihood of the restricted chains.  Synchronous.  Uniform prior only. */
-int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, int32_t lookahead,
+int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, int32_t lookahead, int32_t pool,
                       const int32_t* decode_loci, int32_t D, float* d_out, float lost_tol, float* lost_out,
                       double* pac_out, uint32_t* status_out, int32_t* n_fallback_out, ls_stream_t stream);
 

@@ -135,35 +135,79 @@ def lookahead_sets(S, span=1):
     return U
 
 
-def sparse_posteriors(h, rho, mu, sets, ws, loci):
+def sparse_posteriors(h, rho, mu, sets, ws, loci, pool=False):
     """Posteriors [N, len(loci), N] of the chains restricted to per-window donor sets (sets
-    [N, Wn, K], ascending, -1 padded), prior 1/(N-1) kept, recombination mass to donors outside
-    the set dropped, continuation only for donors in the sets of both loci; 0 outside the set."""
+    [N, Wn, K], ascending, -1 padded), prior 1/(N-1) kept, continuation only for donors in the sets
+    of both loci; 0 outside the set.  pool=False drops the recombination mass that goes to donors
+    outside the set.  pool=True carries those donors as one aggregate state o with their average
+    emission at each locus (count of outside donors sharing the target's allele), o <- theta_out c o
+    + r sum_out theta, adds o to the normalisers, moves the mass of leaving donors into o and starts
+    entering donors at o's average."""
     L, N = h.shape
     pi = 1.0 / (N - 1)
     mu = np.broadcast_to(np.asarray(mu, dtype=np.float64), (L,))
     out = np.zeros((N, len(loci), N))
     slot = {int(l): k for k, l in enumerate(loci)}
+    ones = h.sum(axis=1).astype(np.int64)
 
     def theta(l, i, j):
         return 1.0 - mu[l] if h[l, j] == h[l, i] else mu[l]
 
+    def out_sum(l, i, setl):
+        """(sum of theta over the outside donors, their count) at locus l."""
+        nout = N - 1 - len(setl)
+        mtot = (ones[l] if h[l, i] else N - ones[l]) - 1
+        mset = sum(1 for j in setl if h[l, j] == h[l, i])
+        mout = min(max(mtot - mset, 0), nout)
+        return (1.0 - mu[l]) * mout + mu[l] * (nout - mout), nout
+
+    def move(vals, old, new, o):
+        """values on the set `new` from those on `old`, and the pool after the change."""
+        mapped = sum(vals[j] for j in old if j in new)
+        nout_old = N - 1 - len(old)
+        fill = o / nout_old if (pool and nout_old > 0) else 0.0
+        entering = [j for j in new if j not in old]
+        res = {j: (vals[j] if j in old else fill) for j in new}
+        if pool:
+            o = max(o + (sum(vals.values()) - mapped) - len(entering) * fill, 0.0)
+        return res, o
+
     for i in range(N):
         setof = [[int(j) for j in sets[i, l // ws] if j >= 0] for l in range(L)]
         alpha = [None] * L
+        # forward
         a = {j: theta(0, i, j) * pi for j in setof[0]}
+        ts, no = out_sum(0, i, setof[0])
+        o = pi * ts if pool else 0.0
+        tot = sum(a.values()) + o
         alpha[0] = a
         for l in range(1, L):
-            s = sum(a.values())
-            a = {k: theta(l, i, k) * ((1 - rho[l - 1]) * a.get(k, 0.0) / s + rho[l - 1] * pi) for k in setof[l]}
+            if setof[l] != setof[l - 1]:
+                a, o = move(a, setof[l - 1], setof[l], o)
+            c, r = (1 - rho[l - 1]) / tot, rho[l - 1] * pi
+            a = {k: theta(l, i, k) * (c * a[k] + r) for k in setof[l]}
+            if pool:
+                ts, no = out_sum(l, i, setof[l])
+                o = (ts / no if no > 0 else 0.0) * (c * o) + r * ts
+            tot = sum(a.values()) + o
             alpha[l] = a
+        # backward (t = theta beta)
         t = {j: theta(L - 1, i, j) for j in setof[L - 1]}
         beta = {j: 1.0 for j in setof[L - 1]}
+        ts, no = out_sum(L - 1, i, setof[L - 1])
+        o = ts if pool else 0.0
+        tot = sum(t.values()) + o
         for l in range(L - 1, -1, -1):
             if l < L - 1:
-                S = pi * sum(t.values())
-                beta = {j: (1 - rho[l]) * t.get(j, 0.0) / S + rho[l] for j in setof[l]}
+                if setof[l] != setof[l + 1]:
+                    t, o = move(t, setof[l + 1], setof[l], o)
+                c, r = (1 - rho[l]) / (pi * tot), rho[l]
+                beta = {j: c * t[j] + r for j in setof[l]}
                 t = {j: theta(l, i, j) * beta[j] for j in setof[l]}
+                if pool:
+                    ts, no = out_sum(l, i, setof[l])
+                    o = (ts / no if no > 0 else 0.0) * (c * o) + r * ts
+                tot = sum(t.values()) + o
             if l in slot:
                 z = sum(alpha[l][j] * beta[j] for j in setof[l])
                 for j in setof[l]:

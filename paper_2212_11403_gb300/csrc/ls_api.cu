@@ -1214,7 +1214,7 @@ int run_list(ls_ctx* c, lsk::PropParams p, const int* d_tlist, int nf, cudaStrea
 
 extern "C" {
 
-int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, int32_t lookahead,
+int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, int32_t lookahead, int32_t pool,
                       const int32_t* decode_loci, int32_t D, float* d_out, float lost_tol, float* lost_out,
                       double* pac_out, uint32_t* status_out, int32_t* n_fallback_out, ls_stream_t stream) {
   int rc = check_ctx(ctx);
@@ -1282,6 +1282,14 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
   }
   sp.logs = logs;
   sp.lost = lost;
+  if (pool) {  // per-locus allele counts for the outside pool
+    int32_t* n1;
+    if ((rc = db.get(&n1, L))) return rc;
+    cudaError_t e1 = ls_launch_row_ones(ctx->bits, ctx->row_words, N, L, n1, s);
+    if (e1 != cudaSuccess) return fail(LS_ERR_CUDA, "allele counts: %s", cudaGetErrorString(e1));
+    sp.n1 = n1;
+    sp.pool = 1;
+  }
   cudaError_t e = ls_launch_sparse(0, sp, s);
   if (e != cudaSuccess) return fail(LS_ERR_CUDA, "sparse forward launch: %s", cudaGetErrorString(e));
   for (int k = 0; k < D; ++k) {

@@ -44,3 +44,9 @@ cudaError_t ls_launch_dense_rows_hdist(const float* prod, int nf, int N, const i
   lsk::dense_rows_hdist_kernel<<<dim3(nf, D), 256, 0, s>>>(prod, nf, N, tlist, h);
   return cudaGetLastError();
 }
+
+cudaError_t ls_launch_row_ones(const uint32_t* bits, int row_words, int N, int L, int32_t* n1, cudaStream_t s) {
+  const long long threads = 32ll * L;
+  lsk::row_ones_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(bits, row_words, N, L, n1);
+  return cudaGetLastError();
+}

@@ -13,6 +13,14 @@
 // change is the in-set check: its maximum per target is reported ("lost"), and targets above a
 // tolerance are recomputed densely by the caller.
 //
+// Outside pool (pool = 1): the donors outside the set are carried as one aggregate state o (their
+// total forward mass, or their total t = theta beta backward) with the average emission of the
+// outside donors at each locus (from the locus' allele count minus the set's own matches):
+//   o <- theta_out (c o) + r sum_{j out} theta_j,   theta_out = sum_{j out} theta_j / |out|,
+// and the normalisers become set sum + o, as in the dense chain.  At a window change the mass of
+// donors leaving the set joins the pool and each entering donor takes the pool's average.  Only
+// the posterior mass on outside donors is then missing from the restricted chain.
+//
 // One warp per target, slot s of lane q <-> set index 32 s + q (coalesced set loads and stores);
 // eight targets per CTA share the packed locus rows, staged eight rows at a time in shared memory.
 #pragma once
@@ -45,6 +53,8 @@ struct SparseParams {
   double* logs;          // [N] forward: log-likelihood of the restricted chain (may be null)
   float* lost;           // [N] forward: max normalised mass on leaving donors (may be null)
   uint32_t* status;      // [N] status bits (may be null)
+  const int32_t* n1;     // [L] haplotypes carrying allele 1 at each locus (outside pool only)
+  int pool;              // 1: carry the donors outside the set as one pooled state (below)
 };
 
 __host__ __device__ inline int sparse_smem_bytes(int row_words, int ks) {
@@ -83,9 +93,10 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
     const int q = 32 * s + lane;
     return q < K ? p.idx[((size_t)i * p.Wn + w) * K + q] : -1;
   };
-  // enter window w: map the values of the old set onto the new one (0 for new donors); returns the
-  // mapped total
-  auto enter = [&](int w, bool map) -> float {
+  // enter window w: map the values of the old set onto the new one (`fill` for new donors); returns
+  // the mapped total, and the number of entering donors and of set entries
+  int n_enter = 0, nset = 0;
+  auto enter = [&](int w, bool map, float fill) -> float {
     if (map) {
 #pragma unroll
       for (int s = 0; s < KS; ++s) {
@@ -95,6 +106,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
       __syncwarp();
     }
     float mapped = 0.0f;
+    int ne = 0, nv = 0;
 #pragma unroll
     for (int s = 0; s < KS; ++s) {
       id[s] = set_entry(w, s);
@@ -106,20 +118,31 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
           if (sid[mid] < id[s]) lo = mid + 1;
           else hi = mid;
         }
-        if (lo < 32 * KS && sid[lo] == id[s]) v = sval[lo];
+        if (lo < 32 * KS && sid[lo] == id[s]) {
+          v = sval[lo];
+          mapped += v;
+        } else {
+          v = fill;
+          ++ne;
+        }
       }
+      nv += id[s] >= 0;
       x[s] = v;
-      mapped += v;
     }
     if (map) __syncwarp();
     cur_w = w;
+    n_enter = __reduce_add_sync(0xffffffffu, ne);
+    nset = __reduce_add_sync(0xffffffffu, nv);
     return warp_sum(mapped);
   };
 
   double logacc = 0.0;
   uint32_t stb = 0u;
   float lost_max = 0.0f;
-  float sum_prev = 1.0f;  // forward: sum alpha; backward: sum t over the set
+  float sum_prev = 1.0f;  // forward: sum alpha; backward: sum t (set plus pool)
+  float s_set = 0.0f;     // the set's part of sum_prev
+  float opool = 0.0f;     // outside pool (pool = 1)
+  const int N = p.N;
   int store_next = 0;
   const int nblk = (L + kSparseRows - 1) / kSparseRows;
   for (int b = 0; b < nblk; ++b) {
@@ -143,14 +166,17 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
       const float tm = p.thm[l], tx = p.thx[l];
       float c, r;
       if (cur_w < 0) {  // initial locus: alpha = theta pi ; t = theta (beta = 1)
-        enter(w, false);
+        enter(w, false, 0.0f);
         c = 0.0f;
         r = DIR == 0 ? pi : 1.0f;
       } else {
         const int m = DIR == 0 ? l - 1 : l;  // interval of this transition
         if (w != cur_w) {
-          const float mapped = enter(w, true);
-          if (DIR == 0 && sum_prev > 0.0f) lost_max = fmaxf(lost_max, 1.0f - mapped / sum_prev);
+          const int nout_old = N - 1 - nset;
+          const float fill = (p.pool && nout_old > 0) ? opool / (float)nout_old : 0.0f;
+          const float mapped = enter(w, true, fill);
+          if (DIR == 0 && s_set > 0.0f) lost_max = fmaxf(lost_max, 1.0f - mapped / s_set);
+          if (p.pool) opool = fmaxf(opool + (s_set - mapped) - (float)n_enter * fill, 0.0f);
         }
         if (DIR == 0) {
           c = p.omr[m] / sum_prev;
@@ -166,11 +192,16 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
       float s = 0.0f;
       float zb = 0.0f;  // backward store: sum alpha beta
       float prod[KS];
+      int nmatch = 0;   // set entries matching the target's allele
 #pragma unroll
       for (int q = 0; q < KS; ++q) {
         const int j = id[q];
         float th = 0.0f;
-        if (j >= 0) th = (((row[j >> 5] >> (j & 31)) & 1u) == tb) ? tm : tx;
+        if (j >= 0) {
+          const bool match = ((row[j >> 5] >> (j & 31)) & 1u) == tb;
+          th = match ? tm : tx;
+          nmatch += match;
+        }
         const float u = j >= 0 ? fmaf(c, x[q], r) : 0.0f;  // alpha (fwd) / beta (bwd) before emission
         if (DIR == 1 && is_store) {
           const int sq = 32 * q + lane;
@@ -181,6 +212,18 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
         s += x[q];
       }
       s = warp_sum(s);
+      float tot = s;
+      if (p.pool) {
+        // outside donors: their count, how many match the target here, their summed emission
+        const int n1 = p.n1[l];
+        const int mtot = (tb ? n1 : N - n1) - 1;  // matching donors, the target itself excluded
+        const int nout = N - 1 - nset;
+        const int mout = min(max(mtot - __reduce_add_sync(0xffffffffu, nmatch), 0), nout);
+        const float thsum = tm * (float)mout + tx * (float)(nout - mout);
+        const float thbar = nout > 0 ? thsum / (float)nout : 0.0f;
+        opool = thbar * (c * opool) + r * thsum;
+        tot = s + opool;
+      }
       if (is_store) {
         if (DIR == 0) {
 #pragma unroll
@@ -199,10 +242,11 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
         }
         ++store_next;
       }
-      if (s < 1.17549435e-38f) stb |= 1u;      // LS_STATUS_UNDERFLOW
-      if (!(s <= 3.40282347e+38f)) stb |= 2u;  // LS_STATUS_OVERFLOW (infinite or NaN)
-      if (DIR == 0) logacc += (double)logf(s);
-      sum_prev = s;
+      if (tot < 1.17549435e-38f) stb |= 1u;      // LS_STATUS_UNDERFLOW
+      if (!(tot <= 3.40282347e+38f)) stb |= 2u;  // LS_STATUS_OVERFLOW (infinite or NaN)
+      if (DIR == 0) logacc += (double)logf(tot);
+      s_set = s;
+      sum_prev = tot;
     }
   }
   if (active && lane == 0) {
@@ -291,6 +335,23 @@ __global__ void lookahead_sets_kernel(const int32_t* __restrict__ idx, int N, in
     last = best;
   }
   while (o < width) u[o++] = -1;
+}
+
+// Haplotypes carrying allele 1 at each locus: one warp per row, popcount of the first N bits.
+__global__ void row_ones_kernel(const uint32_t* __restrict__ bits, int row_words, int N, int L, int32_t* __restrict__ n1) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= L) return;
+  const uint32_t* r = bits + (size_t)wid * row_words;
+  int c = 0;
+  for (int k = lane; 32 * k < N; k += 32) {
+    uint32_t v = r[k];
+    const int rem = N - 32 * k;
+    if (rem < 32) v &= (1u << rem) - 1u;
+    c += __popc(v);
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if (lane == 0) n1[wid] = c;
 }
 
 #endif  // LS_SPARSE_PARAMS_ONLY

@@ -100,7 +100,7 @@ def _load():
         "ls_mlp_train": ([P, P, P, ctypes.c_int64, I, I, ctypes.c_float, ctypes.c_uint64, P, P], I),
         "ls_propose_window": ([P, I, I, P, P, P], I),
         "ls_propose": ([P, I, I, P, P, P], I),
-        "ls_sparse_run_all": ([P, P, I, I, I, P, I, P, ctypes.c_float, P, P, P, P, P], I),
+        "ls_sparse_run_all": ([P, P, I, I, I, I, P, I, P, ctypes.c_float, P, P, P, P, P], I),
         "ls_set_profiling": ([P, I], I),
         "ls_profile_read": ([P, P, P], I),
     }
@@ -413,13 +413,13 @@ def ls_propose(ctx, C, K, mlp, idx_out, stream=None):
 
 
 def ls_sparse_run_all(ctx, idx, K, WS, decode_loci, d_out, lost_tol=-1.0, lost_out=None, status_out=None,
-                      lookahead=2, stream=None):
+                      lookahead=2, pool=True, stream=None):
     """Returns (rc, pac of the restricted chains, number of dense-fallback targets)."""
     import torch
     dl = np.ascontiguousarray(decode_loci, dtype=np.int32)
     pac = ctypes.c_double()
     nf = ctypes.c_int32()
-    rc = _check(_lib.ls_sparse_run_all(ctx, _dev(idx, torch.int32, "idx"), int(K), int(WS), int(lookahead),
+    rc = _check(_lib.ls_sparse_run_all(ctx, _dev(idx, torch.int32, "idx"), int(K), int(WS), int(lookahead), int(bool(pool)),
                                        dl.ctypes.data_as(ctypes.c_void_p), dl.size, _dev(d_out, torch.float32, "d_out"),
                                        ctypes.c_float(lost_tol), _dev(lost_out, torch.float32, "lost_out"),
                                        ctypes.byref(pac), _dev(status_out, torch.int32, "status_out"), ctypes.byref(nf),

@@ -249,8 +249,8 @@ def test_trained_proposal_against_raw_counts(ls):
     assert res["mlp"]["mass_q01"] > res["raw"]["mass_q01"]
 
 
-@pytest.mark.parametrize("lookahead", [0, 1, 2])
-def test_restricted_chain_matches_its_oracle(ls, lookahead):
+@pytest.mark.parametrize("lookahead,pool", [(0, False), (1, False), (2, False), (0, True), (2, True)])
+def test_restricted_chain_matches_its_oracle(ls, lookahead, pool):
     """random per-window sets that change between windows: the kernels against the FP64 oracle
     of the restricted chain (oracle/proposal.py sparse_posteriors)."""
     import torch
@@ -269,13 +269,13 @@ def test_restricted_chain_matches_its_oracle(ls, lookahead):
     try:
         ls.ls_set_params(ctx, w["rho"], w["mu"])
         d = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
-        ls.ls_sparse_run_all(ctx, torch.from_numpy(S).cuda(), K, WS, loci, d, lookahead=lookahead)
+        ls.ls_sparse_run_all(ctx, torch.from_numpy(S).cuda(), K, WS, loci, d, lookahead=lookahead, pool=pool)
         torch.cuda.synchronize()
         d = d.cpu().numpy().astype(np.float64)
     finally:
         ls.ls_destroy(ctx)
     sets = op.lookahead_sets(S, lookahead) if lookahead else S
-    p = op.sparse_posteriors(w["h"], w["rho"], w["mu"], sets, WS, loci)
+    p = op.sparse_posteriors(w["h"], w["rho"], w["mu"], sets, WS, loci, pool=pool)
     eps = 2.0 ** -52
     for k, l in enumerate(loci):
         v = l // WS

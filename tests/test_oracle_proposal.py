@@ -112,3 +112,41 @@ def test_lookahead_sets_union():
     assert list(V[0, 0]) == [1, 2, 3, 5] + [-1] * 5
     assert list(V[0, 1]) == [0, 1, 2, 3, 5] + [-1] * 4
     assert list(V[0, 2]) == [0, 2, 3, 5] + [-1] * 5
+
+
+def test_pooled_sparse_oracle_with_full_sets_is_the_dense_oracle():
+    """with every donor in every set the pool is empty and the pooled chain is the dense one."""
+    import oracle
+    rng = np.random.default_rng(19)
+    L, N = 35, 7
+    h = (rng.random((L, N)) < 0.4).astype(np.uint8)
+    rho = rng.uniform(0.01, 0.3, L - 1)
+    sets = np.array([[[j for j in range(N) if j != i]] * 5 for i in range(N)])
+    p = op.sparse_posteriors(h, rho, 0.05, sets, 7, [0, 20, 34], pool=True)
+    ref = oracle.run(h, rho, 0.05, [0, 20, 34], want=("post",))["post"]
+    assert float(np.max(np.abs(p - ref))) < 1e-12
+
+
+def test_pooled_sparse_oracle_is_exact_when_outside_donors_are_identical():
+    """donors outside the set that are all identical to each other (and so share one emission at
+    every locus) are represented exactly by the pool: posteriors of set donors equal the dense
+    oracle's when the outside donors never enter the set."""
+    import oracle
+    rng = np.random.default_rng(23)
+    L, N = 40, 8
+    h = (rng.random((L, N)) < 0.4).astype(np.uint8)
+    h[:, 5] = h[:, 6]
+    h[:, 7] = h[:, 6]
+    rho = rng.uniform(0.01, 0.3, L - 1)
+    i = 0
+    sets = -np.ones((N, 4, 4), dtype=np.int64)
+    sets[i, :, :] = [1, 2, 3, 4]   # outside: 5, 6, 7 (identical)
+    for j in range(1, N):
+        sets[j, :, :N - 1 if N - 1 <= 4 else 4] = [k for k in range(N) if k != j][:4]
+    p = op.sparse_posteriors(h, rho, 0.05, sets, 10, [0, 17, 39], pool=True)
+    ref = oracle.run(h, rho, 0.05, [0, 17, 39], targets=[i], want=("post",))["post"][0]
+    # the pool holds the outside mass exactly, so the set donors' posteriors differ from the dense
+    # ones only by the outside posterior mass, a common factor per locus
+    for k in range(3):
+        ps, pd = p[i, k, 1:5], ref[k, 1:5]
+        np.testing.assert_allclose(ps / ps.sum(), pd / pd.sum(), rtol=1e-12)
