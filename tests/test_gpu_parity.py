@@ -422,3 +422,36 @@ def test_large_n_fallback_rows_match_dense(ls):
     finally:
         ls.ls_destroy(ctx)
     assert d_err(sub, ref.astype(np.float64)) <= 1e-5
+
+
+def test_run_all_on_a_user_stream_and_without_tail_overlap(ls):
+    """a main/tail plan (N=5000: four full waves plus a tail) forks its tail onto a side stream and
+    joins it back; on a caller-created stream, and with the overlap switched off, the results are
+    bit-identical to the default run."""
+    import os
+    import torch
+    w = synth.make_workload("ls_n5000_l20000", N=5000, L=300, seed=5)
+    N = w["N"]
+    loci = np.array([0, 150, 299], dtype=np.int32)
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        d0 = torch.empty((3, N, N), dtype=torch.float32, device="cuda")
+        rc0, pac0 = ls.ls_run_all(ctx, loci, d0)
+        s = torch.cuda.Stream()
+        d1 = torch.full_like(d0, float("nan"))
+        with torch.cuda.stream(s):
+            rc1, pac1 = ls.ls_run_all(ctx, loci, d1, stream=s)
+        s.synchronize()
+        os.environ["LS_TAIL_OVERLAP"] = "0"
+        try:
+            d2 = torch.empty_like(d0)
+            rc2, pac2 = ls.ls_run_all(ctx, loci, d2)
+        finally:
+            del os.environ["LS_TAIL_OVERLAP"]
+        torch.cuda.synchronize()
+        assert rc0 == rc1 == rc2 == 0
+        assert pac0 == pac1 == pac2
+        assert torch.equal(d0, d1) and torch.equal(d0, d2)
+    finally:
+        ls.ls_destroy(ctx)
