@@ -15,8 +15,10 @@
 //
 // Emission.  Per locus the lane turns its donors' bits into "match" bits (XOR with its target's
 // allele); a 16-entry shared-memory table maps 4 match bits to 4 emission probabilities
-// (theta = 1-mu on a match, mu on a mismatch, App. A.3), one 16-byte load per 4 cells, so a
-// cell costs three FP32 operations (FFMA, FMUL, FADD as packed f32x2 pairs).
+// (theta = 1-mu on a match, mu on a mismatch, App. A.3), one 16-byte load per 4 cells; every other
+// quad of 4 cells instead selects theta by a bit test on the integer pipe, which splits the
+// emission fetch between the shared-memory and integer pipes.  A cell costs three FP32 operations
+// (FFMA, FMUL, FADD as packed f32x2 pairs).
 //
 // Padding and diagonal.  Slots beyond the slice and the diagonal slot are forced to "mismatch".
 // Those junk cells all start at 0 and see the same c, r and theta = mu, so they hold one common
@@ -37,6 +39,10 @@ namespace lsk {
 constexpr int kSlots = 3;        // TMA ring slots
 constexpr int kRB = 4;           // consecutive rows per TMA block
 constexpr int kMaxStore = 64;    // store loci per launch
+// every kAluMod-th quad of a lane's slice takes theta by a bit test and select instead of the table
+// (0: none); half of the quads measured fastest on GB300 (the table loads and the selects then
+// share the load between the shared-memory and integer pipes)
+constexpr int kAluMod = 2;
 constexpr float kEps = 2.220446049250313e-16f;  // DBL_EPSILON = 2^-52, exact in FP32 (Eq. distmat)
 
 struct PropParams {
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   int blk_base = 0, blk_n = 0;
   for (int step = 0; step < p.n_steps; ++step) {
     const int l = p.l_first + step_dir * step;
-    const float cur_omr = nx_omr, cur_rr = nx_rr, cur_thx = nx_thx;
+    const float cur_omr = nx_omr, cur_rr = nx_rr, cur_thx = nx_thx, cur_thm = nx_thm;
     if (step + 1 < p.n_steps) {
       const int ln = l + step_dir;
       const int li = DIR == 0 ? ln - 1 : ln;
@@ -568,6 +574,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     // rotating register buffer; a slice word's nibbles are prepared when the lookahead enters it.
     constexpr int kLA = KQ < 4 ? KQ : 4;
     uint32_t hw[2], lw[2];   // 16 x nibble bytes of the words feeding the lookahead (double-buffered)
+    uint32_t mw[2];          // the match words themselves (bit-select quads)
     float4 th[kLA];
     auto prep_word = [&](int m) {
       uint32_t w = funnel(rw[wb + m], rw[wb + m + 1], wsh) ^ inv;  // match bits of 32 slots
@@ -575,6 +582,16 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       if (m == 0) w &= dclear;
       hw[m & 1] = w & 0xf0f0f0f0u;         // 16 x odd nibbles, one per byte
       lw[m & 1] = (w << 4) & 0xf0f0f0f0u;  // 16 x even nibbles
+      mw[m & 1] = w;
+    };
+    // bit-select quads (uniform prior and matrix prior, not the statistic passes, whose second table
+    // is indexed like the first): theta from a bit test and a select instead of a table load
+    auto sel_quad = [&](int k) -> bool { return ST == 0 && kAluMod > 0 && (k % (kAluMod > 0 ? kAluMod : 1)) == kAluMod - 1; };
+    auto sel_th = [&](int k) -> float4 {
+      const uint32_t w = mw[(k >> 3) & 1];
+      const int b = 4 * (k & 7);
+      return make_float4((w >> b) & 1u ? cur_thm : cur_thx, (w >> (b + 1)) & 1u ? cur_thm : cur_thx,
+                         (w >> (b + 2)) & 1u ? cur_thm : cur_thx, (w >> (b + 3)) & 1u ? cur_thm : cur_thx);
     };
     auto load_th = [&](int kk) -> float4 {
       const int q = kk & 7, m = kk >> 3;
@@ -584,14 +601,15 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     };
     prep_word(0);
 #pragma unroll
-    for (int k = 0; k < kLA; ++k) th[k] = load_th(k);
+    for (int k = 0; k < kLA; ++k)
+      if (!sel_quad(k)) th[k] = load_th(k);
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
-      const float4 t = th[k % kLA];
+      const float4 t = sel_quad(k) ? sel_th(k) : th[k % kLA];
       const int kn = k + kLA;
       if (kn < KQ) {
         if ((kn & 7) == 0) prep_word(kn >> 3);
-        th[k % kLA] = load_th(kn);
+        if (!sel_quad(kn)) th[k % kLA] = load_th(kn);
       }
       if (PIM) {
         const float4 pv = *reinterpret_cast<const float4*>(pis + 4 * k);
