@@ -115,7 +115,7 @@ def measure_sparse():
     torch.cuda.synchronize()
     t_train = time.time() - t0
     del X, y
-    for N, judge in ((20000, True), (50000, True)):
+    for N, with_dense in ((20000, True), (50000, True)):
         w = synth.make_workload("ls_n50000_l20000", N=N, seed=6000 + N, founders=N // 25)
         L = w["L"]
         loci = synth.decode_loci(L, 4)
@@ -132,7 +132,7 @@ def measure_sparse():
                 ts = timed(lambda: ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds))
                 rec[name] = dict(propose_seconds=tp, sparse_seconds=ts, total_seconds=tp + ts,
                                  coverage=float(torch.isfinite(ds).float().mean()))
-                if judge:
+                if with_dense:
                     if "dense_seconds" not in rec:
                         dd = torch.empty_like(ds)
                         rec["dense_seconds"] = timed(lambda: ls.ls_run_all(ctx, loci, dd, want_pac=False))
@@ -145,7 +145,7 @@ def measure_sparse():
                                      speedup=rec["dense_seconds"] / (tp + ts))
             out.append(rec)
             del ds
-            if judge:
+            if with_dense:
                 del dd
         finally:
             ls.ls_destroy(ctx)
