@@ -1,0 +1,254 @@
+// ls_hyb.cuh -- dense propagation for large N (uniform prior): one target per CTA of 512 threads,
+// the target's state split between registers and shared memory.
+//
+// Thread t owns donor positions [B t, B (t+1)), B = 4 (QR + QS): its first QR quads of 4 cells stay
+// in registers for all loci, the other QS quads sit in shared memory in quad-major order
+// ([QS][512] float4, so a warp's 16-byte accesses are contiguous).  With QR = 12 the registers hold
+// 24576 positions per target and shared memory up to 16 x 8 KB more (N <= 57344).  Per locus a
+// thread reads the packed bits of its positions from the (L2-resident) packed row one locus ahead,
+// XORs them with the target's allele and selects theta per cell by a bit test (no emission table,
+// so shared-memory traffic is the state of the QS quads only: 8 bytes per cell there, none in the
+// register part), and updates x <- theta (c x + r) with FFMA + FMUL + FADD as f32x2 pairs.
+// Positions beyond N and the target's own position are forced to "mismatch": they all start at 0
+// and see the same c, r and theta = mu, so they hold one common value xs, replicated in every
+// thread, and the row sum subtracts n_junk * xs (the register-tile kernel's treatment).  The row
+// sum is a shuffle tree, one CTA barrier and a 16-entry sum; FP64 log scales are accumulated by
+// thread 0.
+#pragma once
+
+#include "ls_prop.cuh"
+
+namespace lsk {
+
+constexpr int kHybThreads = 512;
+constexpr int kHybQR = 12;  // register quads per thread
+
+template <int QS>
+struct HybCfg {
+  static constexpr int Q = kHybQR + QS;       // quads per thread
+  static constexpr int B = 4 * Q;             // positions per thread
+  static constexpr int NP = kHybThreads * B;  // positions per target (N <= NP)
+  static constexpr int NWA = (B + 31) / 32;   // aligned match words per thread
+  static constexpr int NW = NWA + 1;          // row words read per thread (funnel shift)
+  // dynamic shared memory: the QS shared quads [QS][512], staging of the register quads at store
+  // loci [QR][512] (float4 each), two buffers of 16 warp partials
+  static constexpr int XS_OFF = 0;
+  static constexpr int STG_OFF = XS_OFF + QS * kHybThreads * 16;
+  static constexpr int PART_OFF = STG_OFF + kHybQR * kHybThreads * 16;
+  static constexpr int BYTES = PART_OFF + 2 * 16 * 4;
+  __host__ __device__ static int smem_bytes() { return BYTES; }
+  // beyond the register-tile kernels' range (N <= 20480)
+  __host__ __device__ static bool serves(int N) { return N > 20480 && N <= NP; }
+};
+
+template <int DIR, int QS>
+__global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams p) {
+  using C = HybCfg<QS>;
+  constexpr int QR = kHybQR, Q = C::Q, B = C::B, NWA = C::NWA, NW = C::NW, T = kHybThreads;
+  constexpr int step_dir = DIR == 0 ? 1 : -1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* Xs = reinterpret_cast<float4*>(smem + C::XS_OFF);    // [QS][T] shared quads
+  float4* Stg = reinterpret_cast<float4*>(smem + C::STG_OFF);  // [QR][T] register quads at stores
+  float* part = reinterpret_cast<float*>(smem + C::PART_OFF);  // [2][16]
+  const int N = p.N, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cta_t = p.t_begin + blockIdx.x;  // one target per CTA (or its target-list position)
+  const int tgt = p.tlist ? p.tlist[cta_t] : cta_t;
+  const int row = cta_t - p.tab_t0;
+  const int d0 = B * tid;  // first position of this thread
+  const int w0 = d0 >> 5;
+  const uint32_t sh = (uint32_t)(d0 & 31);
+  const float n_junk = (float)(C::NP - (N - 1));
+
+  // valid positions of the aligned match words: position d0 + 32 k + b is a donor iff it is < N
+  // and not the target (bits beyond the thread's B positions are cleared too)
+  uint32_t vm[NWA];
+#pragma unroll
+  for (int k = 0; k < NWA; ++k) {
+    uint32_t m = 0u;
+    for (int b = 0; b < 32; ++b) {
+      const int o = 32 * k + b, pos = d0 + o;
+      if (o < B && pos < N && pos != tgt) m |= 1u << b;
+    }
+    vm[k] = m;
+  }
+
+  // element e of quad q of thread t: shared or staged location (quad-major)
+  auto elem = [&](int q, int t, int e) -> float* {
+    float4* base = q < QR ? Stg + q * T + t : Xs + (q - QR) * T + t;
+    return reinterpret_cast<float*>(base) + e;
+  };
+
+  f2 x[QR][2];
+#pragma unroll
+  for (int q = 0; q < QR; ++q) x[q][0] = x[q][1] = make_float2(0.f, 0.f);
+  if (p.load_state) {
+    for (int i = tid; i < C::NP; i += T) {
+      const int t = i / B, o = i - t * B;
+      *elem(o >> 2, t, o & 3) = (i < N && i != tgt) ? p.state[(size_t)row * N + i] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < QR; ++q) {
+      const float4 v = Stg[q * T + tid];
+      x[q][0] = make_float2(v.x, v.y);
+      x[q][1] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+  } else {
+    for (int i = tid; i < QS * T; i += T) Xs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+
+  auto reduce = [&](float v, int buf) -> float {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) part[buf * 16 + warp] = v;
+    __syncthreads();
+    float t = part[buf * 16 + (lane & 15)];  // both half-warps sum the 16 partials
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    return t;
+  };
+  // store the row (x, or c x + r when affine) to w1 / multiply m1 by it / w2 (any may be null)
+  auto store_state = [&](float* w1, float* m1, float* w2, bool affine, float c, float r) {
+#pragma unroll
+    for (int q = 0; q < QR; ++q) Stg[q * T + tid] = make_float4(x[q][0].x, x[q][0].y, x[q][1].x, x[q][1].y);
+    __syncthreads();
+    for (int i = tid; i < N; i += T) {
+      const int t = i / B, o = i - t * B;
+      const float xv = *elem(o >> 2, t, o & 3);
+      const float v = i == tgt ? 0.0f : (affine ? fmaf(c, xv, r) : xv);
+      const size_t ro = (size_t)row * N + i;
+      if (w1) w1[ro] = v;
+      if (m1) m1[ro] = i == tgt ? 0.0f : m1[ro] * v;
+      if (w2) w2[ro] = v;
+    }
+    __syncthreads();
+  };
+
+  float sig_prev = 1.0f, xs = 0.0f;
+  if (p.load_state && DIR == 0) {
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < QR; ++q) s += (x[q][0].x + x[q][0].y) + (x[q][1].x + x[q][1].y);
+#pragma unroll
+    for (int q = 0; q < QS; ++q) {
+      const float4 v = Xs[q * T + tid];
+      s += (v.x + v.y) + (v.z + v.w);
+    }
+    sig_prev = reduce(s, 1);
+    __syncthreads();
+  }
+  double lgs = (tid == 0 && p.logs && !p.init) ? p.logs[row] : 0.0;
+  uint32_t sts = 0u;
+  int store_next = 0;
+  int next_store_l = p.n_store > 0 ? p.store_loci[0] : -1;
+  int pend_slot = -1;
+  bool pend_save = false;
+
+  // the row words holding this thread's bits, the target's bit and the locus' emission values,
+  // loaded one locus ahead
+  uint32_t wd[NW], tb;
+  float nthm, nthx;
+  auto load_locus = [&](int l) {
+    const uint32_t* r = p.bits2 + (size_t)l * p.rw2;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) wd[k] = (w0 + k < p.rw2) ? r[w0 + k] : 0u;
+    tb = (r[tgt >> 5] >> (tgt & 31)) & 1u;
+    nthm = p.thm[l];
+    nthx = p.thx[l];
+  };
+  load_locus(p.l_first);
+  for (int step = 0; step < p.n_steps; ++step) {
+    const int l = p.l_first + step_dir * step;
+    uint32_t cw[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) cw[k] = wd[k];
+    const uint32_t ctb = tb;
+    const float thm = nthm, thx = nthx;
+    if (step + 1 < p.n_steps) load_locus(l + step_dir);
+    float c, r;
+    bool add_log_prev = false;
+    const int mi = DIR == 0 ? l - 1 : l;
+    if (step == 0 && p.init) {
+      c = 0.0f;
+      r = DIR == 0 ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
+    } else if (step == 0 && DIR == 1) {
+      c = 1.0f;  // backward resume: x = theta^l beta^l from the stored beta
+      r = 0.0f;
+    } else {
+      c = __fdividef(p.omr[mi], sig_prev);
+      r = p.rr[mi];
+      add_log_prev = DIR == 1;
+    }
+    const bool is_store = l == next_store_l;
+    const bool save_here = p.save_state && step == p.n_steps - 1;
+    if (DIR == 0 && pend_slot >= 0) {  // alpha of the previous locus
+      store_state(p.store + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f);
+      pend_slot = -1;
+    }
+    if (DIR == 1 && (is_store || save_here)) {
+      // beta^l = c t^{l+1} + rho; when decoding, alpha^l beta^l overwrites alpha^l in place
+      const size_t so = (size_t)(is_store ? p.store_slot[store_next] : 0) * p.state_rows * N;
+      store_state((is_store && p.store) ? p.store + so : nullptr, (is_store && p.alpha_dec) ? p.alpha_dec + so : nullptr,
+                  save_here ? p.state : nullptr, true, c, r);
+    }
+
+    // match bits of the thread's positions (bit o of aw[o >> 5] <-> position d0 + o)
+    const uint32_t inv = ctb ? 0u : 0xffffffffu;
+    uint32_t aw[NWA];
+#pragma unroll
+    for (int k = 0; k < NWA; ++k) aw[k] = (funnel(cw[k], cw[k + 1], sh) ^ inv) & vm[k];
+    const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
+    f2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint32_t w = aw[(4 * q) >> 5];
+      const int b = (4 * q) & 31;
+      const f2 t01 = make_float2((w >> b) & 1u ? thm : thx, (w >> (b + 1)) & 1u ? thm : thx);
+      const f2 t23 = make_float2((w >> (b + 2)) & 1u ? thm : thx, (w >> (b + 3)) & 1u ? thm : thx);
+      if (q < QR) {
+        const int qr = q < QR ? q : 0;
+        x[qr][0] = __fmul2_rn(t01, __ffma2_rn(C2, x[qr][0], R2));
+        x[qr][1] = __fmul2_rn(t23, __ffma2_rn(C2, x[qr][1], R2));
+        acc0 = __fadd2_rn(acc0, x[qr][0]);
+        acc1 = __fadd2_rn(acc1, x[qr][1]);
+      } else {
+        float4* sp = Xs + (q - QR) * T + tid;
+        const float4 v = *sp;
+        const f2 y01 = __fmul2_rn(t01, __ffma2_rn(C2, make_float2(v.x, v.y), R2));
+        const f2 y23 = __fmul2_rn(t23, __ffma2_rn(C2, make_float2(v.z, v.w), R2));
+        *sp = make_float4(y01.x, y01.y, y23.x, y23.y);
+        acc0 = __fadd2_rn(acc0, y01);
+        acc1 = __fadd2_rn(acc1, y23);
+      }
+    }
+    xs = thx * fmaf(c, xs, r);  // junk positions: theta = mu everywhere
+
+    if (DIR == 0) {  // alpha^l is stored at the top of the next step (or after the loop)
+      pend_slot = is_store && p.store ? p.store_slot[store_next] : -1;
+      pend_save = save_here;
+    }
+    if (is_store) {
+      ++store_next;
+      next_store_l = store_next < p.n_store ? p.store_loci[store_next] : -1;
+    }
+    float sig = reduce((acc0.x + acc0.y) + (acc1.x + acc1.y), step & 1) - n_junk * xs;
+    if (DIR == 1) sig *= p.pi_u;
+    if (tid == 0) {
+      const float sg = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
+      if (sg < 1.17549435e-38f) sts |= 1u;      // LS_STATUS_UNDERFLOW
+      if (!(sg <= 3.40282347e+38f)) sts |= 2u;  // LS_STATUS_OVERFLOW
+      lgs += (double)logf(sg);
+    }
+    sig_prev = sig;
+  }
+  if (DIR == 0 && (pend_slot >= 0 || pend_save))
+    store_state(pend_slot >= 0 ? p.store + (size_t)pend_slot * p.state_rows * N : nullptr, nullptr,
+                pend_save ? p.state : nullptr, false, 0.f, 0.f);
+  if (tid == 0 && cta_t < p.t_begin + p.t_count) {
+    if (p.logs) p.logs[row] = lgs;
+    if (p.status && sts) atomicOr(p.status + row, sts);
+  }
+}
+
+}  // namespace lsk

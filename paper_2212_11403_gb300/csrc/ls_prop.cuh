@@ -584,9 +584,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       lw[m & 1] = (w << 4) & 0xf0f0f0f0u;  // 16 x even nibbles
       mw[m & 1] = w;
     };
-    // bit-select quads (uniform prior and matrix prior, not the statistic passes, whose second table
-    // is indexed like the first): theta from a bit test and a select instead of a table load
-    auto sel_quad = [&](int k) -> bool { return ST == 0 && kAluMod > 0 && (k % (kAluMod > 0 ? kAluMod : 1)) == kAluMod - 1; };
+    // bit-select quads: theta from a bit test and a select instead of a table load (the statistic
+    // passes' eta H table is still read through the nibble bytes, which every quad keeps)
+    auto sel_quad = [&](int k) -> bool { return kAluMod > 0 && (k % (kAluMod > 0 ? kAluMod : 1)) == kAluMod - 1; };
     auto sel_th = [&](int k) -> float4 {
       const uint32_t w = mw[(k >> 3) & 1];
       const int b = 4 * (k & 7);

@@ -5,7 +5,7 @@
 // given N; the host planner picks the one with the fewest CTA waves x slots per lane.  Variants
 // are spread over translation units (LS_INST_GROUP) so the build compiles them in parallel.
 #include "ls_internal.h"
-#include "ls_smem.cuh"
+#include "ls_hyb.cuh"
 #include "ls_warp.cuh"
 
 namespace {
@@ -50,28 +50,29 @@ bool serves_warp(int N) {
   return lsk::WarpCfg<KQ>::serves(N);
 }
 
-template <int QT>
-cudaError_t launch_smem(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
-  if (dir == 0) lsk::ls_smem_kernel<0, QT><<<grid, lsk::kSmemThreads, smem, s>>>(p);
-  else lsk::ls_smem_kernel<1, QT><<<grid, lsk::kSmemThreads, smem, s>>>(p);
+template <int QS>
+cudaError_t launch_hyb(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
+  if (dir == 0) lsk::ls_hyb_kernel<0, QS><<<grid, lsk::kHybThreads, smem, s>>>(p);
+  else lsk::ls_hyb_kernel<1, QS><<<grid, lsk::kHybThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
-template <int QT>
-int smem_smem(int) {
-  return lsk::SmemCfg<QT>::smem_bytes();
+template <int QS>
+int smem_hyb(int) {
+  return lsk::HybCfg<QS>::smem_bytes();
 }
-template <int QT>
-bool serves_smem(int N) {
-  return lsk::SmemCfg<QT>::serves(N);
+template <int QS>
+bool serves_hyb(int N) {
+  return lsk::HybCfg<QS>::serves(N);
 }
 
 }  // namespace
 
-// large-N variants: one target per CTA of 32 warps, state in shared memory (QT quads per thread)
-#define LS_REGS_SMEM(Q)                                                                             \
-  out.push_back(PropKernelInfo{1, lsk::kSmemThreads / 32, Q, 0, 0,                                  \
-                               {(const void*)lsk::ls_smem_kernel<0, Q>, (const void*)lsk::ls_smem_kernel<1, Q>}, \
-                               launch_smem<Q>, smem_smem<Q>, serves_smem<Q>})
+// large-N variants: one target per CTA of 16 warps, 12 quads per thread in registers and QS in
+// shared memory
+#define LS_REGH(QS)                                                                                 \
+  out.push_back(PropKernelInfo{1, lsk::kHybThreads / 32, lsk::kHybQR + QS, 0, 0,                    \
+                               {(const void*)lsk::ls_hyb_kernel<0, QS>, (const void*)lsk::ls_hyb_kernel<1, QS>}, \
+                               launch_hyb<QS>, smem_hyb<QS>, serves_hyb<QS>})
 
 #define LS_REGW(K)                                                                                  \
   out.push_back(PropKernelInfo{lsk::kWarpTargets, lsk::kWarpTargets, K, 0, 0,                       \
@@ -161,15 +162,21 @@ void ls_register_group11(std::vector<PropKernelInfo>& out) {
 }
 #elif LS_INST_GROUP == 12
 void ls_register_group12(std::vector<PropKernelInfo>& out) {
-  LS_REGS_SMEM(6);
-  LS_REGS_SMEM(8);
-  LS_REGS_SMEM(10);
+  // register + shared-memory state, N in (20480, 40960]
+  LS_REGH(0);
+  LS_REGH(2);
+  LS_REGH(4);
+  LS_REGH(6);
+  LS_REGH(8);
 }
 #elif LS_INST_GROUP == 13
 void ls_register_group13(std::vector<PropKernelInfo>& out) {
-  LS_REGS_SMEM(12);
-  LS_REGS_SMEM(13);
-  LS_REGS_SMEM(14);
+  // N in (40960, 57344]
+  LS_REGH(10);
+  LS_REGH(12);
+  LS_REGH(13);
+  LS_REGH(14);
+  LS_REGH(16);
 }
 #elif LS_INST_GROUP == 8
 void ls_register_group8(std::vector<PropKernelInfo>& out) {

@@ -356,11 +356,11 @@ def test_run_all_n5000_l20000_sampled_targets(ls):
         assert e <= D_TOL, "locus %d: err %.3g" % (loci[k], e)
 
 
-# ---------------------------------------------------------------- large N (state in shared memory)
+# ------------------------------------------------ large N (state in registers and shared memory)
 @pytest.mark.parametrize("N", [20481, 30001, 50000, 57000])
 def test_run_all_large_n_sampled(ls, N):
-    """N beyond the register-tile kernels (one target per CTA, state in shared memory): d among 16
-    sampled targets and their log-likelihoods against the oracle."""
+    """N beyond the register-tile kernels (one target per CTA of 512 threads, state partly in shared
+    memory): d among 16 sampled targets and their log-likelihoods against the oracle."""
     import torch
     L = 40
     w = synth.make_workload("ls_n50000_l20000", N=N, L=L, seed=900 + N % 97, founders=N // 25)
@@ -422,6 +422,38 @@ def test_large_n_fallback_rows_match_dense(ls):
     finally:
         ls.ls_destroy(ctx)
     assert d_err(sub, ref.astype(np.float64)) <= 1e-5
+
+
+@pytest.mark.parametrize("N", [20481, 30001])
+def test_large_n_resume_matches_direct_propagation(ls, N):
+    """large-N kernels (state partly in shared memory) stopped and resumed through a table: the
+    forward 0 -> 20 -> 50 and the backward L-1 -> 35 -> 10 end in the states of direct runs."""
+    import torch
+    L, T0, T1 = 60, 1000, 1064
+    w = synth.make_workload("ls_n50000_l20000", N=N, L=L, seed=31, founders=N // 25)
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        xs = [torch.empty((T1 - T0, N), dtype=torch.float32, device="cuda") for _ in range(4)]
+        lg = [torch.empty(T1 - T0, dtype=torch.float64, device="cuda") for _ in range(4)]
+        for kind, stops, out in ((ls.LS_FWD, ([50], [20, 50]), (0, 1)), (ls.LS_BWD, ([10], [35, 10]), (2, 3))):
+            for path, o in zip(stops, out):
+                t = ls.ls_table_create(ctx, kind, T0, T1)
+                for to in path:
+                    (ls.ls_forward if kind == ls.LS_FWD else ls.ls_backward)(ctx, t, to)
+                ls.ls_table_read(t, state=xs[o], logscale=lg[o])
+                torch.cuda.synchronize()
+                ls.ls_table_destroy(t)
+    finally:
+        ls.ls_destroy(ctx)
+    x = [v.cpu().numpy() for v in xs]
+    g = [v.cpu().numpy() for v in lg]
+    for a, b in ((0, 1), (2, 3)):
+        assert np.all(np.isfinite(x[a])) and x[a].max() > 0
+        np.testing.assert_allclose(x[b], x[a], rtol=1e-5, atol=1e-30)
+        # the resumed run re-sums the loaded state in its own order: FP32 rounding of one normaliser
+        # per locus, about 1e-7 in the log each
+        np.testing.assert_allclose(g[b], g[a], rtol=0, atol=1e-5)
 
 
 def test_run_all_on_a_user_stream_and_without_tail_overlap(ls):
