@@ -22,16 +22,20 @@
 // the posterior mass on outside donors is then missing from the restricted chain.
 //
 // One warp per target, slot s of lane q <-> set index 32 s + q (coalesced set loads and stores);
-// eight targets per CTA share the packed locus rows, staged eight rows at a time in shared memory.
+// eight targets per CTA share the packed locus rows, staged up to eight rows at a time in shared
+// memory together with the rows' per-locus constants, double-buffered: the asynchronous copies
+// (cp.async) of the next block run while the current one is processed.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace lsk {
 
 constexpr int kSparseWarps = 8;  // targets per CTA
-constexpr int kSparseRows = 8;   // rows staged per block
+constexpr int kSparseRows = 8;   // rows staged per block, at most
+constexpr int kSparseScal = 5;   // per-locus constants staged with a row: 1-mu, mu, 1-rho, rho, n1
 
 struct SparseParams {
   const uint32_t* bits;  // packed rows [L][row_words]: haplotype j = bit j%32 of word j/32
@@ -55,11 +59,33 @@ struct SparseParams {
   uint32_t* status;      // [N] status bits (may be null)
   const int32_t* n1;     // [L] haplotypes carrying allele 1 at each locus (outside pool only)
   int pool;              // 1: carry the donors outside the set as one pooled state (below)
+  int rows_per_blk;      // rows staged per block, 1..kSparseRows (sparse_rows_per_blk)
 };
 
-__host__ __device__ inline int sparse_smem_bytes(int row_words, int ks) {
-  return kSparseRows * row_words * 4 + 2 * kSparseWarps * 32 * ks * 4;
+// two row buffers of nr rows and their constants, and the per-warp set copies used at window changes
+__host__ __device__ inline int sparse_smem_bytes_nr(int row_words, int ks, int nr) {
+  return 2 * nr * row_words * 4 + 2 * kSparseScal * kSparseRows * 4 + 2 * kSparseWarps * 32 * ks * 4;
 }
+// the most rows per block (<= kSparseRows) whose buffers fit in 227 KB; 0 if not even one row fits
+__host__ __device__ inline int sparse_rows_per_blk(int row_words, int ks) {
+  for (int nr = kSparseRows; nr >= 1; --nr)
+    if (sparse_smem_bytes_nr(row_words, ks, nr) <= 227 * 1024) return nr;
+  return 0;
+}
+__host__ __device__ inline int sparse_smem_bytes(int row_words, int ks) {
+  return sparse_smem_bytes_nr(row_words, ks, sparse_rows_per_blk(row_words, ks));
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 #ifndef LS_SPARSE_PARAMS_ONLY  // the kernels live in ls_sparse.cu only
 
@@ -69,8 +95,10 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
   constexpr int INF_ID = 0x7fffffff;
   extern __shared__ __align__(16) unsigned char smem[];
   const int rwd = p.row_words;
-  uint32_t* rows = reinterpret_cast<uint32_t*>(smem);
-  int* sid_all = reinterpret_cast<int*>(smem + kSparseRows * rwd * 4);
+  const int NR = p.rows_per_blk;
+  uint32_t* rows = reinterpret_cast<uint32_t*>(smem);                   // [2][NR][rwd]
+  float* scal = reinterpret_cast<float*>(smem + 2 * NR * rwd * 4);     // [2][kSparseScal][kSparseRows]
+  int* sid_all = reinterpret_cast<int*>(scal + 2 * kSparseScal * kSparseRows);
   float* sval_all = reinterpret_cast<float*>(sid_all + kSparseWarps * 32 * KS);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i_raw = p.t_begin + blockIdx.x * kSparseWarps + warp;
@@ -84,6 +112,8 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
   int id[KS];
   float x[KS];
   int cur_w = -1;
+  // padding entries (id -1) are updated like mismatching donors (no per-entry branches in the
+  // locus loop) but never enter a sum, a store or a window map
   auto warp_sum = [&](float v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -144,33 +174,60 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
   float opool = 0.0f;     // outside pool (pool = 1)
   const int N = p.N;
   int store_next = 0;
-  const int nblk = (L + kSparseRows - 1) / kSparseRows;
-  for (int b = 0; b < nblk; ++b) {
-    // loci of this block in processing order: forward ascending, backward descending
-    const int l0 = DIR == 0 ? b * kSparseRows : L - 1 - b * kSparseRows;
-    const int nrows = min(kSparseRows, L - b * kSparseRows);
-    const int base = DIR == 0 ? l0 : l0 - nrows + 1;  // lowest locus of the block
-    __syncthreads();
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(p.bits + (size_t)base * rwd);
-      uint4* dst = reinterpret_cast<uint4*>(rows);
-      const int n16 = nrows * rwd / 4;
-      for (int e = threadIdx.x; e < n16; e += blockDim.x) dst[e] = src[e];
+  const int nblk = (L + NR - 1) / NR;
+  // block b: loci in processing order (forward ascending, backward descending), the lowest of them
+  auto blk = [&](int b, int& l0, int& nrows, int& base) {
+    l0 = DIR == 0 ? b * NR : L - 1 - b * NR;
+    nrows = min(NR, L - b * NR);
+    base = DIR == 0 ? l0 : l0 - nrows + 1;
+  };
+  // asynchronous copies of block b's rows and constants into buffer b & 1 (one commit group)
+  auto issue = [&](int b) {
+    int l0, nrows, base;
+    blk(b, l0, nrows, base);
+    const uint4* src = reinterpret_cast<const uint4*>(p.bits + (size_t)base * rwd);
+    uint4* dst = reinterpret_cast<uint4*>(rows + (b & 1) * NR * rwd);
+    const int n16 = nrows * rwd / 4;
+    for (int e = threadIdx.x; e < n16; e += blockDim.x) cp_async16(dst + e, src + e);
+    const int t = threadIdx.x;
+    if (t < kSparseScal * kSparseRows) {
+      const int f = t / kSparseRows, k = t % kSparseRows, l = base + k;
+      const int m = DIR == 0 ? l - 1 : l;  // interval entering locus l in processing order
+      float* d = scal + ((b & 1) * kSparseScal + f) * kSparseRows + k;
+      if (k < nrows) {
+        if (f == 0) cp_async4(d, p.thm + l);
+        else if (f == 1) cp_async4(d, p.thx + l);
+        else if (f == 2 && m >= 0 && m < L - 1) cp_async4(d, p.omr + m);
+        else if (f == 3 && m >= 0 && m < L - 1) cp_async4(d, p.rho + m);
+        else if (f == 4 && p.n1) cp_async4(d, p.n1 + l);
+      }
     }
-    __syncthreads();
+  };
+  issue(0);
+  cp_async_commit();
+  for (int b = 0; b < nblk; ++b) {
+    int l0, nrows, base;
+    blk(b, l0, nrows, base);
+    __syncthreads();  // every warp is done with block b-1, whose buffer the next copies reuse
+    if (b + 1 < nblk) issue(b + 1);
+    cp_async_commit();
+    cp_async_wait1();  // this thread's copies of block b have landed
+    __syncthreads();   // and everyone's
+    const uint32_t* rowbuf = rows + (b & 1) * NR * rwd;
+    const float* sc = scal + (b & 1) * kSparseScal * kSparseRows;
     for (int k = 0; k < nrows; ++k) {
       const int l = DIR == 0 ? l0 + k : l0 - k;
-      const uint32_t* row = rows + (l - base) * rwd;
+      const int kr = l - base;  // row of locus l in the buffer
+      const uint32_t* row = rowbuf + kr * rwd;
       const int w = l / p.WS;
       const uint32_t tb = (row[i >> 5] >> (i & 31)) & 1u;
-      const float tm = p.thm[l], tx = p.thx[l];
+      const float tm = sc[0 * kSparseRows + kr], tx = sc[1 * kSparseRows + kr];
       float c, r;
       if (cur_w < 0) {  // initial locus: alpha = theta pi ; t = theta (beta = 1)
         enter(w, false, 0.0f);
         c = 0.0f;
         r = DIR == 0 ? pi : 1.0f;
       } else {
-        const int m = DIR == 0 ? l - 1 : l;  // interval of this transition
         if (w != cur_w) {
           const int nout_old = N - 1 - nset;
           const float fill = (p.pool && nout_old > 0) ? opool / (float)nout_old : 0.0f;
@@ -178,13 +235,14 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
           if (DIR == 0 && s_set > 0.0f) lost_max = fmaxf(lost_max, 1.0f - mapped / s_set);
           if (p.pool) opool = fmaxf(opool + (s_set - mapped) - (float)n_enter * fill, 0.0f);
         }
+        const float om = sc[2 * kSparseRows + kr], rh = sc[3 * kSparseRows + kr];  // interval m
         if (DIR == 0) {
-          c = p.omr[m] / sum_prev;
-          r = p.rho[m] * pi;
+          c = om / sum_prev;
+          r = rh * pi;
         } else {
           // S = pi sum_{k in S'} t_k over the set of locus l+1 (the transition's target set)
-          c = p.omr[m] / (pi * sum_prev);
-          r = p.rho[m];
+          c = om / (pi * sum_prev);
+          r = rh;
         }
       }
       const bool is_store = store_next < p.n_store && p.store_loci[store_next] == l;
@@ -193,29 +251,31 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
       float zb = 0.0f;  // backward store: sum alpha beta
       float prod[KS];
       int nmatch = 0;   // set entries matching the target's allele
+      auto body = [&](auto with_store) {
 #pragma unroll
-      for (int q = 0; q < KS; ++q) {
-        const int j = id[q];
-        float th = 0.0f;
-        if (j >= 0) {
-          const bool match = ((row[j >> 5] >> (j & 31)) & 1u) == tb;
-          th = match ? tm : tx;
+        for (int q = 0; q < KS; ++q) {
+          const int j = id[q];
+          const uint32_t wv = row[max(j, 0) >> 5];
+          // bit j of the row (the funnel shift takes the shift modulo 32); padding never matches
+          const bool match = (((__funnelshift_r(wv, wv, (uint32_t)j)) & 1u) == tb) && j >= 0;
           nmatch += match;
+          const float u = fmaf(c, x[q], r);  // alpha (fwd) / beta (bwd) before emission
+          if (decltype(with_store)::value) {
+            const int sq = 32 * q + lane;
+            prod[q] = (sq < K && j >= 0) ? srow[sq] * u : 0.0f;
+            zb += prod[q];
+          }
+          x[q] = (match ? tm : tx) * u;
+          s += j >= 0 ? x[q] : 0.0f;
         }
-        const float u = j >= 0 ? fmaf(c, x[q], r) : 0.0f;  // alpha (fwd) / beta (bwd) before emission
-        if (DIR == 1 && is_store) {
-          const int sq = 32 * q + lane;
-          prod[q] = (sq < K && j >= 0) ? srow[sq] * u : 0.0f;
-          zb += prod[q];
-        }
-        x[q] = th * u;
-        s += x[q];
-      }
+      };
+      if (DIR == 1 && is_store) body(std::true_type{});
+      else body(std::false_type{});
       s = warp_sum(s);
       float tot = s;
       if (p.pool) {
         // outside donors: their count, how many match the target here, their summed emission
-        const int n1 = p.n1[l];
+        const int n1 = __float_as_int(sc[4 * kSparseRows + kr]);
         const int mtot = (tb ? n1 : N - n1) - 1;  // matching donors, the target itself excluded
         const int nout = N - 1 - nset;
         const int mout = min(max(mtot - __reduce_add_sync(0xffffffffu, nmatch), 0), nout);
@@ -229,7 +289,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
 #pragma unroll
           for (int q = 0; q < KS; ++q) {
             const int sq = 32 * q + lane;
-            if (active && sq < K) srow[sq] = x[q];
+            if (active && sq < K) srow[sq] = id[q] >= 0 ? x[q] : 0.0f;  // padding holds its own values
           }
         } else {
           zb = warp_sum(zb);
