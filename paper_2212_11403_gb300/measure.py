@@ -153,14 +153,38 @@ def measure_sparse():
     return out
 
 
+def measure_sparse_case(N, L, K=512):
+    """one sparse forward + backward + distance (raw sets, D = 4) on the N = 50000 generator at a
+    smaller size: the profiling case of the sparse kernels."""
+    import torch
+    w = synth.make_workload("ls_n50000_l20000", N=N, L=L, seed=6000 + N, founders=N // 25)
+    loci = synth.decode_loci(L, 4)
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        idx = torch.empty((N, (L + 255) // 256, K), dtype=torch.int32, device="cuda")
+        ls.ls_propose(ctx, K, K, None, idx)
+        ds = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+        t = timed(lambda: ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds))
+    finally:
+        ls.ls_destroy(ctx)
+    return [dict(workload="ls_n50000_l20000 generator at N=%d L=%d" % (N, L), path="sparse, raw sets", K=K,
+                 seconds=t)]
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["prior", "grad", "sparse"])
+    ap.add_argument("what", choices=["prior", "grad", "sparse", "sparse_case"])
+    ap.add_argument("--N", type=int, default=20000, help="sparse_case: haplotypes")
+    ap.add_argument("--L", type=int, default=2000, help="sparse_case: loci")
     a = ap.parse_args()
     torch.cuda.set_device(0)
-    fn = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse)[a.what]
-    for rec in fn():
+    if a.what == "sparse_case":
+        recs = measure_sparse_case(a.N, a.L)
+    else:
+        recs = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse)[a.what]()
+    for rec in recs:
         print(json.dumps(rec), flush=True)
 
 
