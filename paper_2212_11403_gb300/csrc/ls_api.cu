@@ -1257,10 +1257,16 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
   for (int k = 0; k < D; ++k) wh[k] = decode_loci[k] / WS;
   CUDA_TRY(cudaMemcpyAsync(wos, wh.data(), sizeof(int) * D, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(uint32_t) * N, s));
+  // haplotype-major words: each set entry's 32 bits of a block of loci are one load
+  uint32_t* hw;
+  if ((rc = db.get(&hw, (size_t)((L + 255) / 256) * N * 8))) return rc;
+  {
+    cudaError_t eh = ls_launch_hapmajor(ctx->bits, ctx->row_words, N, L, hw, s);
+    if (eh != cudaSuccess) return fail(LS_ERR_CUDA, "haplotype-major words: %s", cudaGetErrorString(eh));
+  }
   lsk::SparseParams sp;
   memset(&sp, 0, sizeof sp);
-  sp.bits = ctx->bits;
-  sp.row_words = ctx->row_words;
+  sp.hw = hw;
   sp.N = N;
   sp.L = L;
   sp.K = K;

@@ -33,6 +33,7 @@ struct SparseParams;
 }
 cudaError_t ls_launch_sparse(int dir, const lsk::SparseParams& p, cudaStream_t s);
 cudaError_t ls_launch_row_ones(const uint32_t* bits, int row_words, int N, int L, int32_t* n1, cudaStream_t s);
+cudaError_t ls_launch_hapmajor(const uint32_t* bits, int row_words, int N, int L, uint32_t* hw, cudaStream_t s);
 cudaError_t ls_launch_lookahead(const int32_t* idx, int N, int Wn, int K, int span, int32_t* U, cudaStream_t s);
 cudaError_t ls_launch_sparse_hdist(const float* P, const int32_t* idx, int N, int K, int Wn, const int* win_of_slot,
                                    int D, float* h, cudaStream_t s);

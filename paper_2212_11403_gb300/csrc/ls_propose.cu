@@ -395,3 +395,11 @@ int ls_propose(ls_ctx* ctx, int32_t C, int32_t K, const ls_mlp* mlp, int32_t* id
 }
 
 }  // extern "C"
+
+// haplotype-major words of the packed rows: hw [ceil(L/256)][N][8] (the sparse recursions read
+// their donors' bits from it)
+cudaError_t ls_launch_hapmajor(const uint32_t* bits, int row_words, int N, int L, uint32_t* hw, cudaStream_t s) {
+  const int Wn = (L + lsk::kPropWS - 1) / lsk::kPropWS;
+  lsk::hapmajor_kernel<<<dim3((N + 31) / 32, 8, Wn), 32, 0, s>>>(bits, row_words, N, L, hw);
+  return cudaGetLastError();
+}

@@ -5,10 +5,8 @@
 namespace {
 template <int KS>
 cudaError_t launch_ks(int dir, const lsk::SparseParams& p0, cudaStream_t s) {
-  lsk::SparseParams p = p0;
-  p.rows_per_blk = lsk::sparse_rows_per_blk(p.row_words, KS);
-  if (p.rows_per_blk < 1) return cudaErrorInvalidValue;  // a packed row does not fit in shared memory
-  const int smem = lsk::sparse_smem_bytes(p.row_words, KS);
+  const lsk::SparseParams& p = p0;
+  const int smem = lsk::sparse_smem_bytes(KS);
   const void* f = dir == 0 ? (const void*)lsk::ls_sparse_kernel<0, KS> : (const void*)lsk::ls_sparse_kernel<1, KS>;
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -34,12 +34,12 @@
 namespace lsk {
 
 constexpr int kSparseWarps = 8;  // targets per CTA
-constexpr int kSparseRows = 8;   // rows staged per block, at most
-constexpr int kSparseScal = 5;   // per-locus constants staged with a row: 1-mu, mu, 1-rho, rho, n1
+constexpr int kSparseChunk = 32;  // loci per block: one 32-bit haplotype-major word per donor
+constexpr int kSparseScal = 5;    // per-locus constants staged per block: 1-mu, mu, 1-rho, rho, n1
 
 struct SparseParams {
-  const uint32_t* bits;  // packed rows [L][row_words]: haplotype j = bit j%32 of word j/32
-  int row_words;
+  const uint32_t* hw;    // [ceil(L/256)][N][8] haplotype-major words: bit b of word k of (w, j) is
+                         // haplotype j at locus 256 w + 32 k + b (0 beyond L)
   int N, L;
   int K;                 // set entries per target and window
   int WS;                // loci per window
@@ -59,27 +59,13 @@ struct SparseParams {
   uint32_t* status;      // [N] status bits (may be null)
   const int32_t* n1;     // [L] haplotypes carrying allele 1 at each locus (outside pool only)
   int pool;              // 1: carry the donors outside the set as one pooled state (below)
-  int rows_per_blk;      // rows staged per block, 1..kSparseRows (sparse_rows_per_blk)
 };
 
-// two row buffers of nr rows and their constants, and the per-warp set copies used at window changes
-__host__ __device__ inline int sparse_smem_bytes_nr(int row_words, int ks, int nr) {
-  return 2 * nr * row_words * 4 + 2 * kSparseScal * kSparseRows * 4 + 2 * kSparseWarps * 32 * ks * 4;
-}
-// the most rows per block (<= kSparseRows) whose buffers fit in 227 KB; 0 if not even one row fits
-__host__ __device__ inline int sparse_rows_per_blk(int row_words, int ks) {
-  for (int nr = kSparseRows; nr >= 1; --nr)
-    if (sparse_smem_bytes_nr(row_words, ks, nr) <= 227 * 1024) return nr;
-  return 0;
-}
-__host__ __device__ inline int sparse_smem_bytes(int row_words, int ks) {
-  return sparse_smem_bytes_nr(row_words, ks, sparse_rows_per_blk(row_words, ks));
+// two buffers of per-locus constants and the per-warp set copies used at window changes
+__host__ __device__ inline int sparse_smem_bytes(int ks) {
+  return 2 * kSparseScal * kSparseChunk * 4 + 2 * kSparseWarps * 32 * ks * 4;
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
@@ -93,12 +79,10 @@ template <int DIR, int KS>
 __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const SparseParams p) {
   constexpr float eps = 2.220446049250313e-16f;
   constexpr int INF_ID = 0x7fffffff;
+  constexpr int CH = kSparseChunk;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int rwd = p.row_words;
-  const int NR = p.rows_per_blk;
-  uint32_t* rows = reinterpret_cast<uint32_t*>(smem);                   // [2][NR][rwd]
-  float* scal = reinterpret_cast<float*>(smem + 2 * NR * rwd * 4);     // [2][kSparseScal][kSparseRows]
-  int* sid_all = reinterpret_cast<int*>(scal + 2 * kSparseScal * kSparseRows);
+  float* scal = reinterpret_cast<float*>(smem);  // [2][kSparseScal][CH]
+  int* sid_all = reinterpret_cast<int*>(scal + 2 * kSparseScal * CH);
   float* sval_all = reinterpret_cast<float*>(sid_all + kSparseWarps * 32 * KS);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i_raw = p.t_begin + blockIdx.x * kSparseWarps + warp;
@@ -106,14 +90,19 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
   const int i = active ? i_raw : p.t_begin;  // idle warps shadow a valid target and write nothing
   int* sid = sid_all + warp * 32 * KS;
   float* sval = sval_all + warp * 32 * KS;
-  const int K = p.K, L = p.L;
-  const float pi = 1.0f / (float)(p.N - 1);  // dense uniform prior
+  const int K = p.K, L = p.L, N = p.N;
+  const float pi = 1.0f / (float)(N - 1);  // dense uniform prior
 
   int id[KS];
   float x[KS];
+  // mismatch words of the current block: bit k of mm[s] is 1 where entry s's donor differs from the
+  // target at locus 32 b + k.  Padding entries (id -1) get all ones: they are updated like
+  // mismatching donors, all start at 0 when their window starts and so hold one common value xs,
+  // which the row sum subtracts (no per-entry branch in the locus loop).
+  uint32_t mm[KS];
+  uint32_t twd = 0u;  // the target's own word of the block
+  float xs = 0.0f;
   int cur_w = -1;
-  // padding entries (id -1) are updated like mismatching donors (no per-entry branches in the
-  // locus loop) but never enter a sum, a store or a window map
   auto warp_sum = [&](float v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -122,6 +111,20 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
   auto set_entry = [&](int w, int s) -> int {
     const int q = 32 * s + lane;
     return q < K ? p.idx[((size_t)i * p.Wn + w) * K + q] : -1;
+  };
+  // the words of block b (loci 32 b .. 32 b + 31) for the current set
+  auto gather = [&](int b) {
+    const uint32_t* hwb = p.hw + (size_t)(b >> 3) * N * 8 + (b & 7);
+    twd = hwb[(size_t)i * 8];
+#pragma unroll
+    for (int s = 0; s < KS; ++s) mm[s] = id[s] >= 0 ? (hwb[(size_t)id[s] * 8] ^ twd) : 0xffffffffu;
+  };
+  // exact sum of the set's values, in the order the window map sums them
+  auto set_sum = [&]() -> float {
+    float v = 0.0f;
+#pragma unroll
+    for (int s = 0; s < KS; ++s) v += id[s] >= 0 ? x[s] : 0.0f;
+    return warp_sum(v);
   };
   // enter window w: map the values of the old set onto the new one (`fill` for new donors); returns
   // the mapped total, and the number of entering donors and of set entries
@@ -161,6 +164,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
     }
     if (map) __syncwarp();
     cur_w = w;
+    xs = 0.0f;  // every padding entry restarts at 0
     n_enter = __reduce_add_sync(0xffffffffu, ne);
     nset = __reduce_add_sync(0xffffffffu, nv);
     return warp_sum(mapped);
@@ -170,72 +174,58 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
   uint32_t stb = 0u;
   float lost_max = 0.0f;
   float sum_prev = 1.0f;  // forward: sum alpha; backward: sum t (set plus pool)
-  float s_set = 0.0f;     // the set's part of sum_prev
   float opool = 0.0f;     // outside pool (pool = 1)
-  const int N = p.N;
   int store_next = 0;
-  const int nblk = (L + NR - 1) / NR;
-  // block b: loci in processing order (forward ascending, backward descending), the lowest of them
-  auto blk = [&](int b, int& l0, int& nrows, int& base) {
-    l0 = DIR == 0 ? b * NR : L - 1 - b * NR;
-    nrows = min(NR, L - b * NR);
-    base = DIR == 0 ? l0 : l0 - nrows + 1;
-  };
-  // asynchronous copies of block b's rows and constants into buffer b & 1 (one commit group)
-  auto issue = [&](int b) {
-    int l0, nrows, base;
-    blk(b, l0, nrows, base);
-    const uint4* src = reinterpret_cast<const uint4*>(p.bits + (size_t)base * rwd);
-    uint4* dst = reinterpret_cast<uint4*>(rows + (b & 1) * NR * rwd);
-    const int n16 = nrows * rwd / 4;
-    for (int e = threadIdx.x; e < n16; e += blockDim.x) cp_async16(dst + e, src + e);
-    const int t = threadIdx.x;
-    if (t < kSparseScal * kSparseRows) {
-      const int f = t / kSparseRows, k = t % kSparseRows, l = base + k;
+  // blocks of CH loci aligned to multiples of CH, in processing order; the per-locus constants of
+  // the next block are copied asynchronously (cp.async) while the current one is processed
+  const int nb = (L + CH - 1) / CH;
+  auto blk_of = [&](int t) { return DIR == 0 ? t : nb - 1 - t; };
+  auto issue = [&](int t) {
+    const int b = blk_of(t), base = CH * b, nrows = min(CH, L - base);
+    const int f = threadIdx.x / CH, k = threadIdx.x % CH, l = base + k;
+    if (threadIdx.x < kSparseScal * CH && k < nrows) {
       const int m = DIR == 0 ? l - 1 : l;  // interval entering locus l in processing order
-      float* d = scal + ((b & 1) * kSparseScal + f) * kSparseRows + k;
-      if (k < nrows) {
-        if (f == 0) cp_async4(d, p.thm + l);
-        else if (f == 1) cp_async4(d, p.thx + l);
-        else if (f == 2 && m >= 0 && m < L - 1) cp_async4(d, p.omr + m);
-        else if (f == 3 && m >= 0 && m < L - 1) cp_async4(d, p.rho + m);
-        else if (f == 4 && p.n1) cp_async4(d, p.n1 + l);
-      }
+      float* d = scal + ((t & 1) * kSparseScal + f) * CH + k;
+      if (f == 0) cp_async4(d, p.thm + l);
+      else if (f == 1) cp_async4(d, p.thx + l);
+      else if (f == 2 && m >= 0 && m < L - 1) cp_async4(d, p.omr + m);
+      else if (f == 3 && m >= 0 && m < L - 1) cp_async4(d, p.rho + m);
+      else if (f == 4 && p.n1) cp_async4(d, p.n1 + l);
     }
   };
   issue(0);
   cp_async_commit();
-  for (int b = 0; b < nblk; ++b) {
-    int l0, nrows, base;
-    blk(b, l0, nrows, base);
-    __syncthreads();  // every warp is done with block b-1, whose buffer the next copies reuse
-    if (b + 1 < nblk) issue(b + 1);
+  for (int t = 0; t < nb; ++t) {
+    const int b = blk_of(t), base = CH * b, nrows = min(CH, L - base);
+    __syncthreads();  // every warp is done with block t-1, whose buffer the next copies reuse
+    if (t + 1 < nb) issue(t + 1);
     cp_async_commit();
-    cp_async_wait1();  // this thread's copies of block b have landed
+    cp_async_wait1();  // this thread's copies of block t have landed
     __syncthreads();   // and everyone's
-    const uint32_t* rowbuf = rows + (b & 1) * NR * rwd;
-    const float* sc = scal + (b & 1) * kSparseScal * kSparseRows;
-    for (int k = 0; k < nrows; ++k) {
-      const int l = DIR == 0 ? l0 + k : l0 - k;
-      const int kr = l - base;  // row of locus l in the buffer
-      const uint32_t* row = rowbuf + kr * rwd;
+    const float* sc = scal + (t & 1) * kSparseScal * CH;
+    bool need_gather = true;
+    for (int jj = 0; jj < nrows; ++jj) {
+      const int kr = DIR == 0 ? jj : nrows - 1 - jj;  // locus l = base + kr is bit kr of the words
+      const int l = base + kr;
       const int w = l / p.WS;
-      const uint32_t tb = (row[i >> 5] >> (i & 31)) & 1u;
-      const float tm = sc[0 * kSparseRows + kr], tx = sc[1 * kSparseRows + kr];
+      const float tm = sc[0 * CH + kr], tx = sc[1 * CH + kr];
       float c, r;
       if (cur_w < 0) {  // initial locus: alpha = theta pi ; t = theta (beta = 1)
         enter(w, false, 0.0f);
+        need_gather = true;
         c = 0.0f;
         r = DIR == 0 ? pi : 1.0f;
       } else {
         if (w != cur_w) {
+          const float s_set = set_sum();
           const int nout_old = N - 1 - nset;
           const float fill = (p.pool && nout_old > 0) ? opool / (float)nout_old : 0.0f;
           const float mapped = enter(w, true, fill);
           if (DIR == 0 && s_set > 0.0f) lost_max = fmaxf(lost_max, 1.0f - mapped / s_set);
           if (p.pool) opool = fmaxf(opool + (s_set - mapped) - (float)n_enter * fill, 0.0f);
+          need_gather = true;
         }
-        const float om = sc[2 * kSparseRows + kr], rh = sc[3 * kSparseRows + kr];  // interval m
+        const float om = sc[2 * CH + kr], rh = sc[3 * CH + kr];  // interval entering locus l
         if (DIR == 0) {
           c = om / sum_prev;
           r = rh * pi;
@@ -245,37 +235,46 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
           r = rh;
         }
       }
+      if (need_gather) {
+        gather(b);
+        need_gather = false;
+      }
+      const uint32_t tb = (twd >> kr) & 1u;
+      const uint32_t mk = 1u << kr;
       const bool is_store = store_next < p.n_store && p.store_loci[store_next] == l;
-      float* srow = is_store ? p.store + ((size_t)p.store_slot[store_next] * p.N + i) * K : nullptr;
-      float s = 0.0f;
-      float zb = 0.0f;  // backward store: sum alpha beta
-      float prod[KS];
-      int nmatch = 0;   // set entries matching the target's allele
-      auto body = [&](auto with_store) {
+      float* srow = is_store ? p.store + ((size_t)p.store_slot[store_next] * N + i) * K : nullptr;
+      if (DIR == 1 && is_store) {
+        // posterior over the set: alpha (stored by the forward) times beta = c t + r, normalised
+        float zb = 0.0f;
 #pragma unroll
         for (int q = 0; q < KS; ++q) {
-          const int j = id[q];
-          const uint32_t wv = row[max(j, 0) >> 5];
-          // bit j of the row (the funnel shift takes the shift modulo 32); padding never matches
-          const bool match = (((__funnelshift_r(wv, wv, (uint32_t)j)) & 1u) == tb) && j >= 0;
-          nmatch += match;
-          const float u = fmaf(c, x[q], r);  // alpha (fwd) / beta (bwd) before emission
-          if (decltype(with_store)::value) {
-            const int sq = 32 * q + lane;
-            prod[q] = (sq < K && j >= 0) ? srow[sq] * u : 0.0f;
-            zb += prod[q];
-          }
-          x[q] = (match ? tm : tx) * u;
-          s += j >= 0 ? x[q] : 0.0f;
+          const int sq = 32 * q + lane;
+          if (sq < K && id[q] >= 0) zb += srow[sq] * fmaf(c, x[q], r);
         }
-      };
-      if (DIR == 1 && is_store) body(std::true_type{});
-      else body(std::false_type{});
-      s = warp_sum(s);
+        zb = warp_sum(zb);
+        const float inv = zb > 0.0f ? 1.0f / zb : 0.0f;
+#pragma unroll
+        for (int q = 0; q < KS; ++q) {
+          const int sq = 32 * q + lane;
+          if (active && sq < K)
+            srow[sq] = id[q] < 0 ? 0.0f : (zb > 0.0f ? srow[sq] * fmaf(c, x[q], r) * inv : eps);
+        }
+      }
+      float s = 0.0f;
+      int nmatch = 0;  // set entries matching the target's allele
+#pragma unroll
+      for (int q = 0; q < KS; ++q) {
+        const bool mis = (mm[q] & mk) != 0u;
+        nmatch += mis ? 0 : 1;
+        x[q] = (mis ? tx : tm) * fmaf(c, x[q], r);  // theta (c x + r)
+        s += x[q];
+      }
+      xs = tx * fmaf(c, xs, r);
+      s = warp_sum(s) - (float)(32 * KS - nset) * xs;
       float tot = s;
       if (p.pool) {
         // outside donors: their count, how many match the target here, their summed emission
-        const int n1 = __float_as_int(sc[4 * kSparseRows + kr]);
+        const int n1 = __float_as_int(sc[4 * CH + kr]);
         const int mtot = (tb ? n1 : N - n1) - 1;  // matching donors, the target itself excluded
         const int nout = N - 1 - nset;
         const int mout = min(max(mtot - __reduce_add_sync(0xffffffffu, nmatch), 0), nout);
@@ -289,15 +288,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
 #pragma unroll
           for (int q = 0; q < KS; ++q) {
             const int sq = 32 * q + lane;
-            if (active && sq < K) srow[sq] = id[q] >= 0 ? x[q] : 0.0f;  // padding holds its own values
-          }
-        } else {
-          zb = warp_sum(zb);
-          const float inv = zb > 0.0f ? 1.0f / zb : 0.0f;
-#pragma unroll
-          for (int q = 0; q < KS; ++q) {
-            const int sq = 32 * q + lane;
-            if (active && sq < K) srow[sq] = id[q] < 0 ? 0.0f : (zb > 0.0f ? prod[q] * inv : eps);
+            if (active && sq < K) srow[sq] = id[q] >= 0 ? x[q] : 0.0f;
           }
         }
         ++store_next;
@@ -305,7 +296,6 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
       if (tot < 1.17549435e-38f) stb |= 1u;      // LS_STATUS_UNDERFLOW
       if (!(tot <= 3.40282347e+38f)) stb |= 2u;  // LS_STATUS_OVERFLOW (infinite or NaN)
       if (DIR == 0) logacc += (double)logf(tot);
-      s_set = s;
       sum_prev = tot;
     }
   }
