@@ -77,67 +77,111 @@ struct Stage1Args {
   int use[3];  // whether windows w-1, w, w+1 exist
 };
 
-__global__ void stage1_kernel(Stage1Args a, int N, int Np, int C, int32_t* __restrict__ cand,
-                              __nv_bfloat16* __restrict__ feat, float* __restrict__ feat32) {
-  constexpr int NB = 768;
-  __shared__ int hist[NB];
-  __shared__ int wsum[8];
+__global__ void __launch_bounds__(256) stage1_kernel(Stage1Args a, int N, int Np, int C, int32_t* __restrict__ cand,
+                                                     __nv_bfloat16* __restrict__ feat, float* __restrict__ feat32) {
+  constexpr int NB = 768, NT = 256, V = 16;  // score bins, threads, donors per thread per pass step
+  __shared__ int hist[8][NB];                // one histogram per warp (fewer colliding atomics)
+  __shared__ int scan_s[8];
   __shared__ int thr_s, need_eq_s;
-  const int i = blockIdx.x;
-  const uint8_t* r0 = a.Ms[2] + (size_t)i * Np;
-  const uint8_t* r1 = a.Ms[3] + (size_t)i * Np;
-  const uint8_t* r2 = a.Ms[4] + (size_t)i * Np;
-  auto score = [&](int j) -> int {
-    return (a.use[0] ? (int)r0[j] : 0) + (a.use[1] ? (int)r1[j] : 0) + (a.use[2] ? (int)r2[j] : 0);
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // the three windows' rows of target i (16-byte aligned: Np is a multiple of 64)
+  const uint8_t* r0 = a.use[0] ? a.Ms[2] + (size_t)i * Np : nullptr;
+  const uint8_t* r1 = a.use[1] ? a.Ms[3] + (size_t)i * Np : nullptr;
+  const uint8_t* r2 = a.use[2] ? a.Ms[4] + (size_t)i * Np : nullptr;
+  auto load16 = [](const uint8_t* r, int j0) -> uint4 {
+    return r ? *reinterpret_cast<const uint4*>(r + j0) : make_uint4(0u, 0u, 0u, 0u);
   };
-  for (int b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
-  __syncthreads();
-  for (int j = threadIdx.x; j < N; j += blockDim.x)
-    if (j != i) atomicAdd(&hist[score(j)], 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // threshold: the smallest T with #{score <= T} >= C
-    int acc = 0, T = NB - 1, need = 0;
-    for (int b = 0; b < NB; ++b) {
-      if (acc + hist[b] >= C) {
-        T = b;
-        need = C - acc;
-        break;
-      }
-      acc += hist[b];
+  auto byte_of = [](const uint4& v, int k) -> int {
+    const uint32_t w = k < 4 ? v.x : (k < 8 ? v.y : (k < 12 ? v.z : v.w));
+    return (int)((w >> (8 * (k & 3))) & 255u);
+  };
+  // exclusive prefix of v over the block (thread order) and the block total; two barriers
+  auto block_scan = [&](int v, int& total) -> int {
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
     }
-    thr_s = T;
-    need_eq_s = need;
+    if (lane == 31) scan_s[warp] = x;
+    __syncthreads();
+    int wpre = 0, tot = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < 8; ++w2) {
+      const int s = scan_s[w2];
+      wpre += w2 < warp ? s : 0;
+      tot += s;
+    }
+    __syncthreads();
+    total = tot;
+    return wpre + x - v;
+  };
+
+  for (int b = tid; b < 8 * NB; b += NT) (&hist[0][0])[b] = 0;
+  if (tid == 0) {
+    thr_s = NB - 1;  // fewer than C donors: every donor is below the threshold
+    need_eq_s = 0;
+  }
+  __syncthreads();
+  for (int j0 = V * tid; j0 < N; j0 += V * NT) {
+    const uint4 a0 = load16(r0, j0), a1 = load16(r1, j0), a2 = load16(r2, j0);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int j = j0 + k;
+      if (j < N && j != i) atomicAdd(&hist[warp][byte_of(a0, k) + byte_of(a1, k) + byte_of(a2, k)], 1);
+    }
+  }
+  __syncthreads();
+  // threshold: the smallest T with #{score <= T} >= C; thread t owns bins 3t .. 3t+2
+  {
+    int c[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      int s = 0;
+#pragma unroll
+      for (int w2 = 0; w2 < 8; ++w2) s += hist[w2][3 * tid + e];
+      c[e] = s;
+    }
+    int total;
+    int acc = block_scan(c[0] + c[1] + c[2], total);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      if (acc < C && acc + c[e] >= C) {
+        thr_s = 3 * tid + e;
+        need_eq_s = C - acc;
+      }
+      acc += c[e];
+    }
   }
   __syncthreads();
   const int T = thr_s, need_eq = need_eq_s;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int base_sel = 0, base_eq = 0;
-  for (int j0 = 0; j0 < N; j0 += blockDim.x) {
-    const int j = j0 + threadIdx.x;
-    const int sc = (j < N && j != i) ? score(j) : 1 << 30;
-    const bool lt = sc < T, eq = sc == T;
-    // rank of this equal-score donor among equal ones (ascending j)
-    const uint32_t be = __ballot_sync(0xffffffffu, eq);
-    if (lane == 0) wsum[warp] = __popc(be);
-    __syncthreads();
-    int eq_before = base_eq;
-    for (int w2 = 0; w2 < warp; ++w2) eq_before += wsum[w2];
-    eq_before += __popc(be & ((1u << lane) - 1u));
-    int eq_tot = 0;
-    for (int w2 = 0; w2 < 8; ++w2) eq_tot += wsum[w2];
-    __syncthreads();
-    const bool sel = lt || (eq && eq_before < need_eq);
-    const uint32_t bs = __ballot_sync(0xffffffffu, sel);
-    if (lane == 0) wsum[warp] = __popc(bs);
-    __syncthreads();
-    int pos = base_sel;
-    for (int w2 = 0; w2 < warp; ++w2) pos += wsum[w2];
-    pos += __popc(bs & ((1u << lane) - 1u));
-    int sel_tot = 0;
-    for (int w2 = 0; w2 < 8; ++w2) sel_tot += wsum[w2];
-    __syncthreads();
-    if (sel && pos < C) {
+  int base_sel = 0, eq_seen = 0;
+  for (int jc = 0; jc < N; jc += V * NT) {  // the same trip count in every thread (block scans inside)
+    const int j0 = jc + V * tid;
+    uint32_t ltm = 0u, eqm = 0u;  // donors of this thread's 16 below / at the threshold
+    if (j0 < N) {
+      const uint4 a0 = load16(r0, j0), a1 = load16(r1, j0), a2 = load16(r2, j0);
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const int j = j0 + k;
+        const int sc = (j < N && j != i) ? byte_of(a0, k) + byte_of(a1, k) + byte_of(a2, k) : 1 << 30;
+        ltm |= (sc < T ? 1u : 0u) << k;
+        eqm |= (sc == T ? 1u : 0u) << k;
+      }
+    }
+    // equal scores are taken in ascending j until need_eq of them are in
+    int eq_tot;
+    int r = eq_seen + block_scan(__popc(eqm), eq_tot);
+    uint32_t selm = ltm;
+    for (uint32_t m = eqm; m; m &= m - 1u) {
+      if (r < need_eq) selm |= m & (~m + 1u);
+      ++r;
+    }
+    int sel_tot;
+    int pos = base_sel + block_scan(__popc(selm), sel_tot);
+    for (uint32_t m = selm; m; m &= m - 1u, ++pos) {
+      if (pos >= C) break;
+      const int j = j0 + __ffs(m) - 1;
       cand[(size_t)i * C + pos] = j;
       float f[kFeatUsed];
 #pragma unroll
@@ -154,10 +198,10 @@ __global__ void stage1_kernel(Stage1Args a, int N, int Np, int C, int32_t* __res
       }
     }
     base_sel += sel_tot;
-    base_eq += eq_tot;
+    eq_seen += eq_tot;
   }
   // fewer than C donors (C >= N): pad with -1
-  for (int q = base_sel + threadIdx.x; q < C; q += blockDim.x) cand[(size_t)i * C + q] = -1;
+  for (int q = base_sel + tid; q < C; q += NT) cand[(size_t)i * C + q] = -1;
 }
 
 // MLP parameters on the device: BF16 transposed weights for the MMA, FP32 biases.
