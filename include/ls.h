@@ -229,8 +229,10 @@ int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interv
  * with the fewest mismatches over windows w-1..w+1, stage 2 scores them with a 3-layer MLP
  * (8 -> 256 -> 256 -> 1, ReLU) on the match fractions of windows w-3..w+3 and keeps the K best.
  * The recursions of Eq. fwd1 / Eq. bck1 then run over the sets (prior 1/(N-1) as in the dense
- * chain, recombination mass to donors outside the set dropped, continuation only for donors kept
- * across a window change), and targets whose forward mass leaves the sets are recomputed
+ * chain, continuation only for donors kept across a window change); the donors outside the set
+ * are either one pooled state (pool = 1, the default of the Python binding: their mass stays in
+ * the normalisers, leaving donors' mass joins the pool and entering donors start from its
+ * average) or dropped (pool = 0).  Targets whose forward mass leaves the sets are recomputed
  * densely. */
 
 /* Posterior rows (Eq. postprob) from caller-held alpha and beta rows of targets
@@ -293,9 +295,11 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
 
 /* ---- fused pipeline without allocation --------------------------------------------------- */
 
-/* Largest N the allocation-free pipeline accepts: its scratch is a fixed area inside the library
- * sized for this many targets (LS_NOALLOC_MAX_N x 12 bytes plus a few words, about 768 KB, held
- * by every GPU that loads the library until the process exits). */
+/* Largest N the allocation-free pipeline's scratch holds: a fixed area inside the library sized
+ * for this many targets (LS_NOALLOC_MAX_N x 12 bytes plus a few words, about 768 KB, held by every
+ * GPU that loads the library until the process exits).  An N within this bound that no compiled
+ * propagation variant serves is refused by the launch planner (LS_ERR_UNSUPPORTED) before anything
+ * is enqueued, as in ls_run_all. */
 #define LS_NOALLOC_MAX_N 65536
 
 /* The paper has no counterpart to this entry point.  Same computation as ls_run_all (forward and
@@ -310,9 +314,12 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
  * address (cudaGetSymbolAddress) with the context's device current, so make the first call before
  * any stream capture.  All calls share the one area and reuse it: the call clears what must start
  * at zero, and calls whose GPU work overlaps (different streams, or different contexts on one
- * device running at once) race on it.  N > LS_NOALLOC_MAX_N gives LS_ERR_UNSUPPORTED; D is limited
- * to 64 as for ls_run_all.  Synchronous when pac_out is given (it waits for the PAC sum and
- * returns LS_WARN_* like ls_run_all), asynchronous otherwise. */
+ * device running at once) race on it.  It launches exactly the kernels ls_run_all launches (the
+ * same planner), on the caller's stream only.  N > LS_NOALLOC_MAX_N gives LS_ERR_UNSUPPORTED; D is
+ * limited to 64 as for ls_run_all.  Synchronous when pac_out is given (it waits for the PAC sum and
+ * returns LS_WARN_* like ls_run_all), asynchronous otherwise.  A device wait that ran out of time
+ * is recorded in the scratch area and reported as LS_ERR_DEVICE by the next call that passes
+ * pac_out (which then clears the record); calls without pac_out report no device error. */
 int ls_run_all_noalloc(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out, double* pac_out,
                        uint32_t* status_out, ls_stream_t stream);
 

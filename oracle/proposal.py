@@ -3,7 +3,10 @@
 TEST INFRASTRUCTURE ONLY: the product library never imports, links or runs anything here.
 
 The proposal is an extension of the paper's method (the paper runs every target against all
-donors); its definitions, restated from the library's documented contract:
+donors, Sec. 2.1) and has no counterpart there; these are its definitions, written here first and
+pinned by brute force, by the dense oracle where the restricted chain must reduce to it exactly
+(full sets; identical outside donors, an exact lumping), and by an enumeration of the pooled
+chain's paths (tests/test_oracle_proposal.py):
   * window w holds loci [256 w, min(256 (w+1), L)); the mismatch count of haplotypes i, j in w is
     the number of loci of the window where they differ, stored as min(count, 255);
   * stage 1 keeps for target i the C donors j != i with the smallest sum of mismatch counts over

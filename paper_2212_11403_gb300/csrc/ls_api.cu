@@ -105,17 +105,24 @@ struct Cand {
   int smem, per_sm;
 };
 
-std::vector<Cand> candidates(ls_ctx* c) {
-  std::vector<Cand> out;
+// Upper bound on compiled variants (the registry is a fixed list; the planner keeps its candidates
+// in fixed arrays so that the allocation-free pipeline shares it).
+constexpr int kMaxCand = 64;
+
+// Every compiled propagation variant (no statistic passes) that serves N with the context's prior
+// kind, fits the shared-memory limit and can be resident.  LS_PROP_VARIANT="tpw,w,kq" keeps only
+// that variant: a measurement switch for tuning sweeps, honoured by every entry point alike.
+int candidates(ls_ctx* c, Cand* out, int* nout) {
+  *nout = 0;
   const int N = c->N;
   const int pim = c->Pi ? 1 : 0;
-  // the one-warp-per-target kernels are opt-in (LS_WARP=1): measured slower than the CTA kernels
-  // at N = 5000 (no CTA barrier, but the same issue-bound loop with fewer targets sharing a row load)
-  const char* wenv = getenv("LS_WARP");
-  const bool allow_warp = wenv && wenv[0] == '1';
+  int pa = 0, pb = 0, pk = 0;
+  const char* ov = getenv("LS_PROP_VARIANT");
+  const bool pin = ov && sscanf(ov, "%d,%d,%d", &pa, &pb, &pk) == 3;
   for (const auto& k : registry()) {
+    if (*nout >= kMaxCand) break;
     if (k.st != 0 || k.pim != pim || !k.serves(N)) continue;
-    if (k.warp && !allow_warp) continue;
+    if (pin && !(k.tpw == pa && k.w == pb && k.kq == pk)) continue;
     const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;
     bool ok = true;
@@ -127,9 +134,13 @@ std::vector<Cand> candidates(ls_ctx* c) {
       cudaGetLastError();
       continue;
     }
-    out.push_back(Cand{&k, smem, nb});
+    out[(*nout)++] = Cand{&k, smem, nb};
   }
-  return out;
+  if (*nout == 0) {
+    if (pin) return fail(LS_ERR_UNSUPPORTED, "LS_PROP_VARIANT=%s does not serve N=%d", ov, N);
+    return fail(LS_ERR_UNSUPPORTED, "no compiled propagation variant serves N=%d", N);
+  }
+  return LS_OK;
 }
 
 // modelled time of one launch: for every wave, (CTAs per SM in that wave) x warps x (slots per
@@ -139,17 +150,17 @@ double cost_of(const Cand& cd, int count, int nsm) {
   const long long per_wave = (long long)nsm * cd.per_sm;
   const long long full = ctas / per_wave, rem = ctas % per_wave;
   // fewer than two warps per scheduler leave the dependent FP32 chain exposed: count it double
-  double unit = cd.k->w * (cd.k->kq + 3.0) * (cd.per_sm * cd.k->w < 8 ? 2.0 : 1.0);
-  if (cd.k->warp) unit *= 0.5;  // when enabled, preferred wherever it serves N
+  const double unit = cd.k->w * (cd.k->kq + 3.0) * (cd.per_sm * cd.k->w < 8 ? 2.0 : 1.0);
   double t = (double)full * cd.per_sm * unit;
   if (rem) t += (double)((rem + nsm - 1) / nsm) * unit;
   return t;
 }
 
-const Cand* best_for(const std::vector<Cand>& cs, int count, int nsm, double* cost) {
+const Cand* best_for(const Cand* cs, int nc, int count, int nsm, double* cost) {
   const Cand* best = nullptr;
   double bc = 1e300;
-  for (const auto& cd : cs) {
+  for (int i = 0; i < nc; ++i) {
+    const Cand& cd = cs[i];
     const double cc = cost_of(cd, count, nsm);
     if (cc < bc * 0.999 || (cc <= bc * 1.001 && best && cd.k->tpw > best->k->tpw)) {
       bc = cc;
@@ -160,39 +171,33 @@ const Cand* best_for(const std::vector<Cand>& cs, int count, int nsm, double* co
   return best;
 }
 
-int plan(ls_ctx* c, int t_begin, int t_count, std::vector<Launch>& out) {
-  out.clear();
-  auto cs = candidates(c);
-  if (cs.empty()) return fail(LS_ERR_UNSUPPORTED, "no compiled propagation variant serves N=%d", c->N);
-  // LS_PROP_VARIANT="tpw,w,kq" restricts the planner to one compiled variant (tuning sweeps)
-  if (const char* ov = getenv("LS_PROP_VARIANT")) {
-    int a = 0, b = 0, k = 0;
-    if (sscanf(ov, "%d,%d,%d", &a, &b, &k) == 3) {
-      std::vector<Cand> keep;
-      for (const auto& cd : cs)
-        if (cd.k->tpw == a && cd.k->w == b && cd.k->kq == k) keep.push_back(cd);
-      if (keep.empty()) return fail(LS_ERR_UNSUPPORTED, "LS_PROP_VARIANT=%s does not serve N=%d", ov, c->N);
-      cs = keep;
-    }
-  }
+// Launch plan for targets [t_begin, t_begin + t_count): full waves of the best variant, then the
+// remainder with the variant best for it when that is cheaper.  At most two launches; no heap use
+// (the allocation-free pipeline plans with it too).
+int plan(ls_ctx* c, int t_begin, int t_count, Launch* out, int* nout) {
+  *nout = 0;
+  Cand cs[kMaxCand];
+  int nc = 0;
+  int rc = candidates(c, cs, &nc);
+  if (rc) return rc;
   double c1 = 0;
-  const Cand* b1 = best_for(cs, t_count, c->num_sms, &c1);
-  // full waves of the best variant, then the remainder with the variant best for it
+  const Cand* b1 = best_for(cs, nc, t_count, c->num_sms, &c1);
   const int per_wave_t = c->num_sms * b1->per_sm * b1->k->tpw;
   if (t_count > per_wave_t && t_count % per_wave_t != 0) {
     const int main_t = (t_count / per_wave_t) * per_wave_t;
-    double cm = 0, ct = 0;
-    const Cand* bm = b1;
-    cm = cost_of(*bm, main_t, c->num_sms);
-    const Cand* bt = best_for(cs, t_count - main_t, c->num_sms, &ct);
+    double ct = 0;
+    const double cm = cost_of(*b1, main_t, c->num_sms);
+    const Cand* bt = best_for(cs, nc, t_count - main_t, c->num_sms, &ct);
     if (cm + ct < c1) {
-      out.push_back(Launch{bm->k, t_begin, main_t, main_t / bm->k->tpw, bm->smem});
       const int tt = t_count - main_t;
-      out.push_back(Launch{bt->k, t_begin + main_t, tt, (tt + bt->k->tpw - 1) / bt->k->tpw, bt->smem});
+      out[0] = Launch{b1->k, t_begin, main_t, main_t / b1->k->tpw, b1->smem};
+      out[1] = Launch{bt->k, t_begin + main_t, tt, (tt + bt->k->tpw - 1) / bt->k->tpw, bt->smem};
+      *nout = 2;
       return LS_OK;
     }
   }
-  out.push_back(Launch{b1->k, t_begin, t_count, (t_count + b1->k->tpw - 1) / b1->k->tpw, b1->smem});
+  out[0] = Launch{b1->k, t_begin, t_count, (t_count + b1->k->tpw - 1) / b1->k->tpw, b1->smem};
+  *nout = 1;
   return LS_OK;
 }
 
@@ -215,14 +220,16 @@ void base_params(ls_ctx* c, lsk::PropParams& p, int dir) {
 }
 
 int run_launches(ls_ctx* c, lsk::PropParams p, int t_begin, int t_count, cudaStream_t s, int* nlaunch = nullptr) {
-  std::vector<Launch> lp;
-  int rc = plan(c, t_begin, t_count, lp);
+  Launch lp[2];
+  int nlp = 0;
+  int rc = plan(c, t_begin, t_count, lp, &nlp);
   if (rc) return rc;
-  if (nlaunch) *nlaunch = (int)lp.size();
+  if (nlaunch) *nlaunch = nlp;
   // A main/tail plan: the tail (few targets, one small CTA per SM, latency-bound) goes first on a
   // side stream so that its CTAs share SMs with the main waves instead of running after them.
+  // LS_TAIL_OVERLAP=0 (a measurement switch) runs both on the caller's stream, in order.
   const char* ov = getenv("LS_TAIL_OVERLAP");
-  if (lp.size() == 2 && !(ov && ov[0] == '0')) {
+  if (nlp == 2 && !(ov && ov[0] == '0')) {
     if (!c->side) {
       CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
       CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
@@ -242,7 +249,8 @@ int run_launches(ls_ctx* c, lsk::PropParams p, int t_begin, int t_count, cudaStr
     CUDA_TRY(cudaStreamWaitEvent(s, c->join_ev, 0));
     return LS_OK;
   }
-  for (const auto& L : lp) {
+  for (int i = 0; i < nlp; ++i) {
+    const Launch& L = lp[i];
     p.t_begin = L.t_begin;
     p.t_count = L.t_count;
     cudaError_t e = L.k->launch(p.dir, p, L.grid, L.smem, s);
@@ -1196,13 +1204,15 @@ int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interv
 namespace {
 // dense propagation of a list of targets (one target per CTA), for the fallback rows
 int run_list(ls_ctx* c, lsk::PropParams p, const int* d_tlist, int nf, cudaStream_t s) {
-  auto cs = candidates(c);
-  std::vector<Cand> one;
-  for (const auto& cd : cs)
-    if (cd.k->tpw == 1) one.push_back(cd);
-  if (one.empty()) return fail(LS_ERR_UNSUPPORTED, "no one-target propagation variant serves N=%d", c->N);
+  Cand cs[kMaxCand], one[kMaxCand];
+  int nc = 0, no = 0;
+  int rc = candidates(c, cs, &nc);
+  if (rc) return rc;
+  for (int i = 0; i < nc; ++i)
+    if (cs[i].k->tpw == 1) one[no++] = cs[i];
+  if (no == 0) return fail(LS_ERR_UNSUPPORTED, "no one-target propagation variant serves N=%d", c->N);
   double cost = 0;
-  const Cand* b = best_for(one, nf, c->num_sms, &cost);
+  const Cand* b = best_for(one, no, nf, c->num_sms, &cost);
   p.tlist = d_tlist;
   p.t_begin = 0;
   p.t_count = nf;
@@ -1475,65 +1485,6 @@ __global__ void pac_reduce_kernel(const double* __restrict__ logF, const uint32_
   }
 }
 
-// Launch plan with fixed-size arrays (no heap use on this path).
-int plan_fixed(ls_ctx* c, int t_count, Launch* out, int* nout) {
-  struct C2 {
-    const PropKernelInfo* k;
-    int smem, per_sm;
-  };
-  C2 cs[64];
-  int nc = 0;
-  for (const auto& k : registry()) {
-    if (nc >= 64) break;
-    if (k.st != 0 || k.pim != (c->Pi ? 1 : 0) || !k.serves(c->N)) continue;
-    const int smem = k.smem_bytes(c->rw2);
-    if (smem > 227 * 1024) continue;
-    bool ok = true;
-    for (int d = 0; d < 2 && ok; ++d)
-      if (cudaFuncSetAttribute(k.func[d], cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) ok = false;
-    int nb = 0;
-    if (ok && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.func[0], k.w * 32, smem) != cudaSuccess || nb < 1)) ok = false;
-    if (!ok) {
-      cudaGetLastError();
-      continue;
-    }
-    cs[nc++] = C2{&k, smem, nb};
-  }
-  if (!nc) return fail(LS_ERR_UNSUPPORTED, "no compiled propagation variant serves N=%d", c->N);
-  auto best = [&](int count, double* cost) {
-    int bi = 0;
-    double bc = 1e300;
-    for (int i = 0; i < nc; ++i) {
-      const double cc = cost_of(Cand{cs[i].k, cs[i].smem, cs[i].per_sm}, count, c->num_sms);
-      if (cc < bc * 0.999 || (cc <= bc * 1.001 && cs[i].k->tpw > cs[bi].k->tpw)) {
-        bc = cc;
-        bi = i;
-      }
-    }
-    *cost = bc;
-    return bi;
-  };
-  double c1 = 0, cm = 0, ct = 0;
-  const int b1 = best(t_count, &c1);
-  const int per_wave_t = c->num_sms * cs[b1].per_sm * cs[b1].k->tpw;
-  *nout = 0;
-  if (t_count > per_wave_t && t_count % per_wave_t != 0) {
-    const int main_t = (t_count / per_wave_t) * per_wave_t;
-    cm = cost_of(Cand{cs[b1].k, cs[b1].smem, cs[b1].per_sm}, main_t, c->num_sms);
-    const int bt = best(t_count - main_t, &ct);
-    if (cm + ct < c1) {
-      const int tt = t_count - main_t;
-      out[0] = Launch{cs[b1].k, 0, main_t, main_t / cs[b1].k->tpw, cs[b1].smem};
-      out[1] = Launch{cs[bt].k, main_t, tt, (tt + cs[bt].k->tpw - 1) / cs[bt].k->tpw, cs[bt].smem};
-      *nout = 2;
-      return LS_OK;
-    }
-  }
-  out[0] = Launch{cs[b1].k, 0, t_count, (t_count + cs[b1].k->tpw - 1) / cs[b1].k->tpw, cs[b1].smem};
-  *nout = 1;
-  return LS_OK;
-}
-
 }  // namespace
 
 extern "C" int ls_run_all_noalloc(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out, double* pac_out,
@@ -1552,15 +1503,18 @@ extern "C" int ls_run_all_noalloc(ls_ctx* ctx, const int32_t* decode_loci, int32
     if (k && decode_loci[k] <= decode_loci[k - 1]) return fail(LS_ERR_ARG, "decode loci must be strictly increasing");
   }
   if (D > 0 && !is_device_ptr(d_out)) return fail(LS_ERR_ARG, "ls_run_all_noalloc needs d_out in device memory");
+  // the same launch plan as ls_run_all (one planner, fixed arrays); planned before anything is
+  // enqueued, so that an N no variant serves is refused with nothing queued
+  Launch lp[2];
+  int nl = 0;
+  if ((rc = plan(ctx, 0, N, lp, &nl))) return rc;
   NoallocScratch* sc = nullptr;
   if ((rc = noalloc_scratch(ctx->device, &sc))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  // what must start at zero: the status words and the error word (log F is written in full)
+  // what must start at zero: the status words (log F is written in full).  The error word is not
+  // cleared here: a timed-out wait of an earlier asynchronous call stays recorded until a call
+  // with pac_out reads (and then clears) it.
   CUDA_TRY(cudaMemsetAsync(sc->status, 0, sizeof(uint32_t) * N, s));
-  CUDA_TRY(cudaMemsetAsync(&sc->err, 0, sizeof(int), s));
-  Launch lp[2];
-  int nl = 0;
-  if ((rc = plan_fixed(ctx, N, lp, &nl))) return rc;
   for (int dir = 0; dir < 2; ++dir) {
     lsk::PropParams p;
     base_params(ctx, p, dir);
@@ -1607,7 +1561,11 @@ extern "C" int ls_run_all_noalloc(ls_ctx* ctx, const int32_t* decode_loci, int32
   CUDA_TRY(cudaMemcpyAsync(&any, &sc->any, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(&err, &sc->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
-  if (err) return fail(LS_ERR_DEVICE, "a device wait for staged haplotype rows ran out of time");
+  if (err) {
+    CUDA_TRY(cudaMemsetAsync(&sc->err, 0, sizeof(int), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return fail(LS_ERR_DEVICE, "a device wait for staged haplotype rows ran out of time (this or an earlier call)");
+  }
   *pac_out = pac;
   if (any & 1u) return LS_WARN_UNDERFLOW;
   if (any & 2u) return LS_WARN_OVERFLOW;

@@ -18,7 +18,6 @@ struct PropKernelInfo {
   cudaError_t (*launch)(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s);
   int (*smem_bytes)(int rw2);
   bool (*serves)(int N);
-  int warp = 0;  // 1: one-warp-per-target kernel (ls_warp_kernel)
 };
 
 void ls_register_prop_kernels(std::vector<PropKernelInfo>& out);

@@ -6,7 +6,6 @@
 // are spread over translation units (LS_INST_GROUP) so the build compiles them in parallel.
 #include "ls_internal.h"
 #include "ls_hyb.cuh"
-#include "ls_warp.cuh"
 
 namespace {
 
@@ -35,21 +34,6 @@ bool serves_prop(int N) {
   return lsk::PropCfg<TPW, W, KQ>::serves(N);
 }
 
-template <int KQ>
-cudaError_t launch_warp(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
-  if (dir == 0) lsk::ls_warp_kernel<0, KQ><<<grid, lsk::kWarpTargets * 32, smem, s>>>(p);
-  else lsk::ls_warp_kernel<1, KQ><<<grid, lsk::kWarpTargets * 32, smem, s>>>(p);
-  return cudaGetLastError();
-}
-template <int KQ>
-int smem_warp(int rw2) {
-  return lsk::WarpCfg<KQ>::smem_bytes(rw2);
-}
-template <int KQ>
-bool serves_warp(int N) {
-  return lsk::WarpCfg<KQ>::serves(N);
-}
-
 template <int QS>
 cudaError_t launch_hyb(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
   if (dir == 0) lsk::ls_hyb_kernel<0, QS><<<grid, lsk::kHybThreads, smem, s>>>(p);
@@ -73,11 +57,6 @@ bool serves_hyb(int N) {
   out.push_back(PropKernelInfo{1, lsk::kHybThreads / 32, lsk::kHybQR + QS, 0, 0,                    \
                                {(const void*)lsk::ls_hyb_kernel<0, QS>, (const void*)lsk::ls_hyb_kernel<1, QS>}, \
                                launch_hyb<QS>, smem_hyb<QS>, serves_hyb<QS>})
-
-#define LS_REGW(K)                                                                                  \
-  out.push_back(PropKernelInfo{lsk::kWarpTargets, lsk::kWarpTargets, K, 0, 0,                       \
-                               {(const void*)lsk::ls_warp_kernel<0, K>, (const void*)lsk::ls_warp_kernel<1, K>}, \
-                               launch_warp<K>, smem_warp<K>, serves_warp<K>, 1})
 
 #define LS_REGP(T, Wp, K, P)                                                                        \
   out.push_back(PropKernelInfo{T, Wp, K, P, 0,                                                      \
@@ -148,18 +127,9 @@ void ls_register_group7(std::vector<PropKernelInfo>& out) {
   LS_REGP(8, 4, 16, 1);
 }
 #elif LS_INST_GROUP == 10
-void ls_register_group10(std::vector<PropKernelInfo>& out) {
-  // one warp per target: N <= 5120
-  LS_REGW(40);
-  LS_REGW(32);
-  LS_REGW(24);
-}
+void ls_register_group10(std::vector<PropKernelInfo>&) {}
 #elif LS_INST_GROUP == 11
-void ls_register_group11(std::vector<PropKernelInfo>& out) {
-  LS_REGW(16);
-  LS_REGW(8);
-  LS_REGW(4);
-}
+void ls_register_group11(std::vector<PropKernelInfo>&) {}
 #elif LS_INST_GROUP == 12
 void ls_register_group12(std::vector<PropKernelInfo>& out) {
   // register + shared-memory state, N in (20480, 40960]

@@ -26,8 +26,10 @@ def ls():
 
 
 def d_err(dg, dr):
+    """per-entry error of distances: max over entries of |d_gpu - d_ref| / max(|d_ref|, 1)."""
     dg = np.asarray(dg, dtype=np.float64)
-    return float(np.max(np.abs(dg - dr)) / max(1.0, float(np.max(np.abs(dr)))))
+    dr = np.asarray(dr, dtype=np.float64)
+    return float(np.max(np.abs(dg - dr) / np.maximum(np.abs(dr), 1.0)))
 
 
 def full_sets(N, Wn):

@@ -150,3 +150,79 @@ def test_pooled_sparse_oracle_is_exact_when_outside_donors_are_identical():
     for k in range(3):
         ps, pd = p[i, k, 1:5], ref[k, 1:5]
         np.testing.assert_allclose(ps / ps.sum(), pd / pd.sum(), rtol=1e-12)
+
+
+def _changing_sets(N, Wn, base, extra_choices, i, rng):
+    """sets [N, Wn, K] for target i: base donors plus, per window, a different subset of
+    extra_choices (never i); other targets get all donors but themselves (unused)."""
+    K = N - 1
+    sets = -np.ones((N, Wn, K), dtype=np.int64)
+    for t in range(N):
+        sets[t, :, :N - 1] = [k for k in range(N) if k != t]
+    for w in range(Wn):
+        pick = [j for j in extra_choices if j != i and rng.random() < 0.5]
+        s = sorted(set(j for j in base if j != i) | set(pick))
+        sets[i, w, :] = -1
+        sets[i, w, :len(s)] = s
+    return sets
+
+
+def test_pooled_chain_is_an_exact_lumping_with_changing_sets():
+    """Donors outside the set all identical (one shared haplotype, hence one emission at every
+    locus): by symmetry the dense chain gives them equal alpha and beta, so the pool holds their
+    mass exactly, a donor that leaves hands its mass to the pool, and an entering donor's
+    pool share is its dense value.  The pooled chain is then an exact lumping of the dense chain
+    even as donors of the identical group enter and leave the set between windows, and the set
+    donors' posteriors equal the dense ones divided by the dense posterior mass of the set."""
+    import oracle
+    rng = np.random.default_rng(41)
+    L, N, ws = 36, 10, 4
+    Wn = (L + ws - 1) // ws
+    h = (rng.random((L, N)) < 0.45).astype(np.uint8)
+    G = [5, 6, 7, 8, 9]
+    for g in G[1:]:
+        h[:, g] = h[:, G[0]]
+    rho = rng.uniform(0.02, 0.4, L - 1)
+    mu = 0.07
+    loci = [0, 3, 4, 9, 17, 26, 35]
+    for i in (0, 2, 6):   # targets outside and inside the identical group
+        sets = _changing_sets(N, Wn, [0, 1, 2, 3, 4], G, i, rng)
+        changes = sum(1 for w in range(1, Wn) if list(sets[i, w]) != list(sets[i, w - 1]))
+        assert changes >= 3
+        p = op.sparse_posteriors(h, rho, mu, sets, ws, loci, pool=True)[i]
+        ref = oracle.run(h, rho, mu, loci, targets=[i], want=("post",))["post"][0]
+        for k, l in enumerate(loci):
+            S = [int(j) for j in sets[i, l // ws] if j >= 0]
+            want = ref[k, S] / ref[k, S].sum()
+            np.testing.assert_allclose(p[k, S], want, rtol=1e-12, atol=0)
+
+
+def test_pooled_chain_matches_brute_force_of_its_definition():
+    """Arbitrary haplotypes (the pool is then only an approximation of the dense chain): the
+    oracle's pooled recursions, window changes included, against an enumeration of every path
+    of the pooled chain written out as an explicit HMM (tests/_brute.py)."""
+    from tests._brute import enumerate_pooled
+    rng = np.random.default_rng(43)
+    for trial in range(4):
+        L, N, ws = 6, 5, 2
+        Wn = 3
+        h = (rng.random((L, N)) < 0.5).astype(np.uint8)
+        rho = rng.uniform(0.05, 0.6, L - 1)
+        mu = rng.uniform(0.02, 0.2)
+        i = trial % N
+        others = [j for j in range(N) if j != i]
+        sets = -np.ones((N, Wn, N - 1), dtype=np.int64)
+        for t in range(N):
+            sets[t, :, :N - 1] = [k for k in range(N) if k != t]
+        chosen = [[others[0], others[1]], [others[1], others[2]], [others[0], others[3]]]
+        for w in range(Wn):
+            sets[i, w, :] = -1
+            sets[i, w, :2] = sorted(chosen[w])
+        loci = list(range(L))
+        p = op.sparse_posteriors(h, rho, mu, sets, ws, loci, pool=True)[i]
+        marg = enumerate_pooled(h, rho, mu, [[int(j) for j in sets[i, l // ws] if j >= 0] for l in range(L)], i)
+        for l in range(L):
+            S = [int(j) for j in sets[i, l // ws] if j >= 0]
+            z = sum(marg[l].get(j, 0.0) for j in S)
+            for j in S:
+                assert abs(p[l, j] - marg[l].get(j, 0.0) / z) <= 1e-12, (trial, l, j)
