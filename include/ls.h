@@ -216,8 +216,10 @@ int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out,
  * this one is the score by the Fisher identity (posterior expectation of the complete-data score
  * of Eq. transition and App. A.3's emission), computed by two forward statistic passes and one
  * backward pass in FP32 with FP64 sums.  Outputs are host doubles (any may be NULL); dlogrho has
- * K entries, 0 for groups without intervals.  Device memory: 3 * (number of nonempty groups) *
- * T * N floats + 2 * T * N floats, allocated for the call and freed before it returns.
+ * K entries, 0 for groups without intervals.  Device memory: (3 * (number of nonempty groups) + 2)
+ * floats per target and donor, allocated for the call and freed before it returns; the targets
+ * are processed in blocks whose scratch stays within 16 GiB (the environment variable
+ * LS_GRAD_BUDGET_MB, a positive number of MiB, sets another ceiling; one target is the minimum).
  * Synchronous.  Requires the uniform prior (LS_ERR_UNSUPPORTED otherwise), rho < 1 and mu < 1.
  * Returns LS_WARN_* like ls_run_all. */
 int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interval_of, int32_t K,

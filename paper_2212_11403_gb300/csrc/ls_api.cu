@@ -146,7 +146,7 @@ int candidates(ls_ctx* c, Cand* out, int* nout) {
 // modelled time of one launch: for every wave, (CTAs per SM in that wave) x warps x (slots per
 // lane + a fixed per-locus overhead), summed over waves
 double cost_of(const Cand& cd, int count, int nsm) {
-  const long long ctas = (count + cd.k->tpw - 1) / cd.k->tpw;
+  const long long ctas = (long long)((count + cd.k->tpw - 1) / cd.k->tpw) * cd.k->cpt;
   const long long per_wave = (long long)nsm * cd.per_sm;
   const long long full = ctas / per_wave, rem = ctas % per_wave;
   // fewer than two warps per scheduler leave the dependent FP32 chain exposed: count it double
@@ -182,7 +182,7 @@ int plan(ls_ctx* c, int t_begin, int t_count, Launch* out, int* nout) {
   if (rc) return rc;
   double c1 = 0;
   const Cand* b1 = best_for(cs, nc, t_count, c->num_sms, &c1);
-  const int per_wave_t = c->num_sms * b1->per_sm * b1->k->tpw;
+  const int per_wave_t = std::max(1, c->num_sms * b1->per_sm * b1->k->tpw / b1->k->cpt);
   if (t_count > per_wave_t && t_count % per_wave_t != 0) {
     const int main_t = (t_count / per_wave_t) * per_wave_t;
     double ct = 0;
@@ -1023,6 +1023,117 @@ struct DevBufs {
     return rc;
   }
 };
+// Device scratch ceiling of ls_pac_grad (targets are processed in blocks that fit it): 16 GiB, or
+// the environment variable LS_GRAD_BUDGET_MB when it is set to a positive number of MiB.
+size_t grad_budget() {
+  const char* e = getenv("LS_GRAD_BUDGET_MB");
+  const long long mb = e ? atoll(e) : 0;
+  return mb > 0 ? (size_t)mb << 20 : (size_t)16 << 30;
+}
+
+// One block of targets [b0, b0 + TB) of ls_pac_grad: the two forward statistic passes and the
+// backward pass, then the per-group sums of the block (sums [G + 2]: G recombination statistics,
+// the mismatch statistic, the log-likelihood) and the status words of the block in stat.
+int grad_block(ls_ctx* ctx, const StatPick& sp, int b0, int TB, int L, int G, const std::vector<int>& ge,
+               const std::vector<float>& eta, const float* d_gam, const float* d_eta, const uint8_t* d_rst, float* A,
+               float* Wst, float* B, float* xst, float* wst, double* logF, double* EM, double* Rg, double* sums,
+               uint32_t* stat, cudaStream_t s) {
+  const int N = ctx->N;
+  int rc = LS_OK;
+  CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(uint32_t) * TB, s));
+  const int grid = (TB + sp.k->tpw - 1) / sp.k->tpw;
+  auto launch = [&](int which, lsk::PropParams& p) -> int {
+    p.t_begin = b0;
+    p.t_count = TB;
+    cudaError_t e = sp.k->launch(which, p, grid, sp.smem, s);
+    if (e != cudaSuccess) return fail(LS_ERR_CUDA, "statistic pass launch: %s", cudaGetErrorString(e));
+    return LS_OK;
+  };
+  // forward statistic pass 1 (recombinations per group), alpha and w stored at the group ends,
+  // in launches of at most kMaxStore stores that carry alpha and w between them
+  {
+    int k0 = 0, pos = -1;
+    do {
+      const int k1 = std::min(G, k0 + lsk::kMaxStore);
+      const int seg_end = k1 < G ? ge[k1 - 1] : L - 1;
+      lsk::PropParams p;
+      base_params(ctx, p, 0);
+      p.l_first = pos + 1;
+      p.n_steps = seg_end - pos;
+      p.init = pos < 0 ? 1 : 0;
+      p.load_state = pos < 0 ? 0 : 1;
+      p.save_state = 1;
+      p.tab_t0 = b0;
+      p.state_rows = TB;
+      p.state = xst;
+      p.wstate = wst;
+      p.logs = logF;
+      p.status = stat;
+      p.gam = d_gam;
+      p.reset = d_rst;
+      p.n_store = k1 - k0;
+      for (int k = k0; k < k1; ++k) {
+        p.store_loci[k - k0] = ge[k];
+        p.store_slot[k - k0] = k;
+      }
+      p.store = A;
+      p.wstore = Wst;
+      if ((rc = launch(0, p))) return rc;
+      pos = seg_end;
+      k0 = k1;
+    } while (pos < L - 1);
+  }
+  // forward statistic pass 2 (mismatches), read at the last locus
+  {
+    lsk::PropParams p;
+    base_params(ctx, p, 0);
+    p.l_first = 0;
+    p.n_steps = L;
+    p.init = 1;
+    p.tab_t0 = b0;
+    p.state_rows = TB;
+    p.eta = eta[0];
+    p.eta_vec = ctx->mu_vec ? d_eta : nullptr;
+    p.stat_out = EM;
+    if ((rc = launch(1, p))) return rc;
+  }
+  // backward: beta at the group ends (decreasing), in launches of at most kMaxStore stores
+  if (G > 0) {
+    int k0 = 0, pos = L;  // stores are taken in the order e_{G-1}, ..., e_0
+    do {
+      const int k1 = std::min(G, k0 + lsk::kMaxStore);
+      const int seg_end = ge[G - k1];  // the lowest store locus of this launch
+      lsk::PropParams p;
+      base_params(ctx, p, 1);
+      p.l_first = pos == L ? L - 1 : pos;
+      p.n_steps = p.l_first - seg_end + 1;
+      p.init = pos == L ? 1 : 0;
+      p.load_state = pos == L ? 0 : 1;
+      p.save_state = 1;
+      p.tab_t0 = b0;
+      p.state_rows = TB;
+      p.state = xst;
+      p.n_store = k1 - k0;
+      for (int k = k0; k < k1; ++k) {
+        p.store_loci[k - k0] = ge[G - 1 - k];
+        p.store_slot[k - k0] = G - 1 - k;
+      }
+      p.store = B;
+      if ((rc = run_launches(ctx, p, b0, TB, s))) return rc;
+      pos = seg_end;
+      k0 = k1;
+    } while (k0 < G);
+    lsk::grad_dot_kernel<<<dim3(TB, G), 256, 0, s>>>(A, Wst, B, N, TB, Rg);
+    CUDA_TRY(cudaGetLastError());
+    lsk::sum_rows_kernel<<<G, 256, 0, s>>>(Rg, TB, sums);
+    CUDA_TRY(cudaGetLastError());
+  }
+  lsk::sum_rows_kernel<<<1, 256, 0, s>>>(EM, TB, sums + G);
+  CUDA_TRY(cudaGetLastError());
+  lsk::sum_rows_kernel<<<1, 256, 0, s>>>(logF, TB, sums + G + 1);
+  CUDA_TRY(cudaGetLastError());
+  return LS_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1064,117 +1175,46 @@ int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interv
     rst[m] = (m == 0 || interval_of[m] != interval_of[m - 1]) ? 1 : 0;
   }
   for (int l = 0; l < L; ++l) eta[l] = (float)(1.0 / (1.0 - ctx->mu_h[ctx->mu_h.size() > 1 ? l : 0]));
+  // Targets are processed in blocks whose device scratch (alpha, w and beta at every group end, plus
+  // the carried alpha and w: (3 G + 2) floats per target and donor) stays within kGradBudget bytes;
+  // blocks are whole waves of the statistic kernel where possible.
+  const size_t per_target = ((size_t)3 * G + 2) * (size_t)N * sizeof(float);
+  int Tb = (int)std::min<size_t>((size_t)T, std::max<size_t>(1, grad_budget() / per_target));
+  if (Tb < T) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sp.k->func[0], sp.k->w * 32, sp.smem);
+    const int wave = std::max(1, nb) * ctx->num_sms * sp.k->tpw;
+    if (Tb >= wave) Tb = (Tb / wave) * wave;
+  }
+  Tb = std::min(Tb, T);
   DevBufs db;
   float *d_gam, *d_eta, *A, *Wst, *B, *xst, *wst;
   uint8_t* d_rst;
   double *logF, *EM, *Rg, *sums;
   uint32_t* stat;
-  const size_t TN = (size_t)T * N;
+  const size_t TN = (size_t)Tb * N;
   if ((rc = db.get(&d_gam, gam.size())) || (rc = db.get(&d_eta, eta.size())) || (rc = db.get(&d_rst, rst.size())) ||
       (rc = db.get(&A, (size_t)G * TN)) || (rc = db.get(&Wst, (size_t)G * TN)) || (rc = db.get(&B, (size_t)G * TN)) ||
-      (rc = db.get(&xst, TN)) || (rc = db.get(&wst, TN)) || (rc = db.get(&logF, T)) || (rc = db.get(&EM, T)) ||
-      (rc = db.get(&Rg, (size_t)std::max(G, 1) * T)) || (rc = db.get(&sums, (size_t)G + 2)) || (rc = db.get(&stat, T)))
+      (rc = db.get(&xst, TN)) || (rc = db.get(&wst, TN)) || (rc = db.get(&logF, Tb)) || (rc = db.get(&EM, Tb)) ||
+      (rc = db.get(&Rg, (size_t)std::max(G, 1) * Tb)) || (rc = db.get(&sums, (size_t)G + 2)) || (rc = db.get(&stat, Tb)))
     return rc;
   CUDA_TRY(cudaMemcpyAsync(d_gam, gam.data(), sizeof(float) * gam.size(), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(d_eta, eta.data(), sizeof(float) * eta.size(), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(d_rst, rst.data(), rst.size(), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(uint32_t) * T, s));
-  const int grid = (T + sp.k->tpw - 1) / sp.k->tpw;
-  auto launch = [&](int which, lsk::PropParams& p) -> int {
-    p.t_begin = t_from;
-    p.t_count = T;
-    cudaError_t e = sp.k->launch(which, p, grid, sp.smem, s);
-    if (e != cudaSuccess) return fail(LS_ERR_CUDA, "statistic pass launch: %s", cudaGetErrorString(e));
-    return LS_OK;
-  };
-  // forward statistic pass 1 (recombinations per group), alpha and w stored at the group ends,
-  // in launches of at most kMaxStore stores that carry alpha and w between them
-  {
-    int k0 = 0, pos = -1;
-    do {
-      const int k1 = std::min(G, k0 + lsk::kMaxStore);
-      const int seg_end = k1 < G ? ge[k1 - 1] : L - 1;
-      lsk::PropParams p;
-      base_params(ctx, p, 0);
-      p.l_first = pos + 1;
-      p.n_steps = seg_end - pos;
-      p.init = pos < 0 ? 1 : 0;
-      p.load_state = pos < 0 ? 0 : 1;
-      p.save_state = 1;
-      p.tab_t0 = t_from;
-      p.state_rows = T;
-      p.state = xst;
-      p.wstate = wst;
-      p.logs = logF;
-      p.status = stat;
-      p.gam = d_gam;
-      p.reset = d_rst;
-      p.n_store = k1 - k0;
-      for (int k = k0; k < k1; ++k) {
-        p.store_loci[k - k0] = ge[k];
-        p.store_slot[k - k0] = k;
-      }
-      p.store = A;
-      p.wstore = Wst;
-      if ((rc = launch(0, p))) return rc;
-      pos = seg_end;
-      k0 = k1;
-    } while (pos < L - 1);
+  std::vector<double> hs(G + 2, 0.0), hb(G + 2);
+  std::vector<uint32_t> sh(Tb);
+  uint32_t any = 0;
+  for (int b0 = t_from; b0 < t_to; b0 += Tb) {
+    const int TB = std::min(Tb, t_to - b0);
+    if ((rc = grad_block(ctx, sp, b0, TB, L, G, ge, eta, d_gam, d_eta, d_rst, A, Wst, B, xst, wst, logF, EM, Rg, sums,
+                         stat, s)))
+      return rc;
+    CUDA_TRY(cudaMemcpyAsync(hb.data(), sums, sizeof(double) * (G + 2), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(sh.data(), stat, sizeof(uint32_t) * TB, cudaMemcpyDeviceToHost, s));
+    if ((rc = read_err_word(ctx, s))) return rc;
+    for (int g = 0; g < G + 2; ++g) hs[g] += hb[g];
+    for (int r = 0; r < TB; ++r) any |= sh[r];
   }
-  // forward statistic pass 2 (mismatches), read at the last locus
-  {
-    lsk::PropParams p;
-    base_params(ctx, p, 0);
-    p.l_first = 0;
-    p.n_steps = L;
-    p.init = 1;
-    p.tab_t0 = t_from;
-    p.state_rows = T;
-    p.eta = eta[0];
-    p.eta_vec = ctx->mu_vec ? d_eta : nullptr;
-    p.stat_out = EM;
-    if ((rc = launch(1, p))) return rc;
-  }
-  // backward: beta at the group ends (decreasing), in launches of at most kMaxStore stores
-  if (G > 0) {
-    int k0 = 0, pos = L;  // stores are taken in the order e_{G-1}, ..., e_0
-    do {
-      const int k1 = std::min(G, k0 + lsk::kMaxStore);
-      const int seg_end = ge[G - k1];  // the lowest store locus of this launch
-      lsk::PropParams p;
-      base_params(ctx, p, 1);
-      p.l_first = pos == L ? L - 1 : pos;
-      p.n_steps = p.l_first - seg_end + 1;
-      p.init = pos == L ? 1 : 0;
-      p.load_state = pos == L ? 0 : 1;
-      p.save_state = 1;
-      p.tab_t0 = t_from;
-      p.state_rows = T;
-      p.state = xst;
-      p.n_store = k1 - k0;
-      for (int k = k0; k < k1; ++k) {
-        p.store_loci[k - k0] = ge[G - 1 - k];
-        p.store_slot[k - k0] = G - 1 - k;
-      }
-      p.store = B;
-      if ((rc = run_launches(ctx, p, t_from, T, s))) return rc;
-      pos = seg_end;
-      k0 = k1;
-    } while (k0 < G);
-    lsk::grad_dot_kernel<<<dim3(T, G), 256, 0, s>>>(A, Wst, B, N, T, Rg);
-    CUDA_TRY(cudaGetLastError());
-    lsk::sum_rows_kernel<<<G, 256, 0, s>>>(Rg, T, sums);
-    CUDA_TRY(cudaGetLastError());
-  }
-  lsk::sum_rows_kernel<<<1, 256, 0, s>>>(EM, T, sums + G);
-  CUDA_TRY(cudaGetLastError());
-  lsk::sum_rows_kernel<<<1, 256, 0, s>>>(logF, T, sums + G + 1);
-  CUDA_TRY(cudaGetLastError());
-  std::vector<double> hs(G + 2);
-  std::vector<uint32_t> sh(T);
-  CUDA_TRY(cudaMemcpyAsync(hs.data(), sums, sizeof(double) * (G + 2), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaMemcpyAsync(sh.data(), stat, sizeof(uint32_t) * T, cudaMemcpyDeviceToHost, s));
-  if ((rc = read_err_word(ctx, s))) return rc;
   // constant terms of the scores, FP64 on the host
   if (dlogrho_out) {
     for (int k = 0; k < K; ++k) dlogrho_out[k] = 0.0;
@@ -1191,8 +1231,6 @@ int ls_pac_grad(ls_ctx* ctx, int32_t t_from, int32_t t_to, const int32_t* interv
     *dlogmu_out = hs[G] - (double)T * cm;
   }
   if (pac_out) *pac_out = hs[G + 1];
-  uint32_t any = 0;
-  for (auto v : sh) any |= v;
   if (any & 1u) return LS_WARN_UNDERFLOW;
   if (any & 2u) return LS_WARN_OVERFLOW;
   return LS_OK;

@@ -56,7 +56,7 @@ __global__ void posterior_kernel(const float* __restrict__ alpha, const float* _
   const float* b = beta + (size_t)r * N;
   float s = 0.0f;
   for (int j = threadIdx.x; j < N; j += blockDim.x)
-    if (j != i) s += a[j] * b[j];
+    if (j != i) s += a[j] * (b[j] * kProdScale);
   __shared__ float red[32];
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -71,7 +71,7 @@ __global__ void posterior_kernel(const float* __restrict__ alpha, const float* _
   const float invZ = Z > 0.0f ? 1.0f / Z : 0.0f;
   float* o = out + (size_t)r * N;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    float p = j == i ? 0.0f : (Z > 0.0f ? a[j] * b[j] * invZ : eps);
+    float p = j == i ? 0.0f : (Z > 0.0f ? a[j] * (b[j] * kProdScale) * invZ : eps);
     if (mode == 1) p = j == i ? 0.0f : -0.5f * logf(fmaxf(p, eps));
     o[j] = p;
   }

@@ -14,6 +14,12 @@
 // thread, and the row sum subtracts n_junk * xs (the register-tile kernel's treatment).  The row
 // sum is a shuffle tree, one CTA barrier and a 16-entry sum; FP64 log scales are accumulated by
 // thread 0.
+//
+// Cluster variant (CL = 2, N up to 2 x 57344): a target's positions are split between the two CTAs
+// of a thread-block cluster on two SMs, CTA rank r holding positions [r NP, (r+1) NP).  Per locus
+// every warp writes its partial sum into both CTAs' shared memory (distributed shared memory), one
+// cluster barrier publishes them, and both CTAs add the 32 partials in the same fixed order, so they
+// hold bit-identical normalisers.
 #pragma once
 
 #include "ls_prop.cuh"
@@ -22,6 +28,23 @@ namespace lsk {
 
 constexpr int kHybThreads = 512;
 constexpr int kHybQR = 12;  // register quads per thread
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// all threads of every CTA of the cluster; release/acquire order shared-memory writes (local and
+// remote) before the barrier with reads after it
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// store v at the same shared-memory offset as `local` in CTA `rank` of the cluster
+__device__ __forceinline__ void st_cluster(float* local, uint32_t rank, float v) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
+}
 
 template <int QS>
 struct HybCfg {
@@ -35,29 +58,36 @@ struct HybCfg {
   static constexpr int XS_OFF = 0;
   static constexpr int STG_OFF = XS_OFF + QS * kHybThreads * 16;
   static constexpr int PART_OFF = STG_OFF + kHybQR * kHybThreads * 16;
-  static constexpr int BYTES = PART_OFF + 2 * 16 * 4;
+  static constexpr int BYTES = PART_OFF + 2 * 32 * 4;
   __host__ __device__ static int smem_bytes() { return BYTES; }
-  // beyond the register-tile kernels' range (N <= 20480)
-  __host__ __device__ static bool serves(int N) { return N > 20480 && N <= NP; }
+  // beyond the register-tile kernels' range (N <= 20480); with CL CTAs per target, beyond the
+  // one-CTA range (N <= 57344)
+  __host__ __device__ static bool serves(int N, int CL = 1) {
+    return CL == 1 ? (N > 20480 && N <= NP) : (N > 57344 && N <= CL * NP);
+  }
 };
 
-template <int DIR, int QS>
+template <int DIR, int QS, int CL>
 __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams p) {
+  static_assert(CL == 1 || CL == 2, "one CTA or a cluster of two per target");
   using C = HybCfg<QS>;
   constexpr int QR = kHybQR, Q = C::Q, B = C::B, NWA = C::NWA, NW = C::NW, T = kHybThreads;
   constexpr int step_dir = DIR == 0 ? 1 : -1;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* Xs = reinterpret_cast<float4*>(smem + C::XS_OFF);    // [QS][T] shared quads
   float4* Stg = reinterpret_cast<float4*>(smem + C::STG_OFF);  // [QR][T] register quads at stores
-  float* part = reinterpret_cast<float*>(smem + C::PART_OFF);  // [2][16]
+  float* part = reinterpret_cast<float*>(smem + C::PART_OFF);  // [2][32]
   const int N = p.N, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int cta_t = p.t_begin + blockIdx.x;  // one target per CTA (or its target-list position)
+  const int rank = CL == 2 ? (int)cluster_rank() : 0;
+  const int cta_t = p.t_begin + blockIdx.x / CL;  // one target per CTA or cluster (or its list position)
   const int tgt = p.tlist ? p.tlist[cta_t] : cta_t;
   const int row = cta_t - p.tab_t0;
-  const int d0 = B * tid;  // first position of this thread
+  const int pos0 = rank * C::NP;  // first position of this CTA
+  const int d0 = pos0 + B * tid;  // first position of this thread
   const int w0 = d0 >> 5;
   const uint32_t sh = (uint32_t)(d0 & 31);
-  const float n_junk = (float)(C::NP - (N - 1));
+  const float n_junk = (float)(CL * C::NP - (N - 1));
+  if (CL == 2) cluster_sync();  // both CTAs are running before any remote shared-memory store
 
   // valid positions of the aligned match words: position d0 + 32 k + b is a donor iff it is < N
   // and not the target (bits beyond the thread's B positions are cleared too)
@@ -83,8 +113,8 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   for (int q = 0; q < QR; ++q) x[q][0] = x[q][1] = make_float2(0.f, 0.f);
   if (p.load_state) {
     for (int i = tid; i < C::NP; i += T) {
-      const int t = i / B, o = i - t * B;
-      *elem(o >> 2, t, o & 3) = (i < N && i != tgt) ? p.state[(size_t)row * N + i] : 0.0f;
+      const int t = i / B, o = i - t * B, g = pos0 + i;
+      *elem(o >> 2, t, o & 3) = (g < N && g != tgt) ? p.state[(size_t)row * N + g] : 0.0f;
     }
     __syncthreads();
 #pragma unroll
@@ -101,11 +131,24 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   auto reduce = [&](float v, int buf) -> float {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) part[buf * 16 + warp] = v;
-    __syncthreads();
-    float t = part[buf * 16 + (lane & 15)];  // both half-warps sum the 16 partials
+    if (CL == 1) {
+      if (lane == 0) part[buf * 32 + warp] = v;
+      __syncthreads();
+      float t = part[buf * 32 + (lane & 15)];  // both half-warps sum the 16 partials
 #pragma unroll
-    for (int off = 8; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      for (int off = 8; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      return t;
+    }
+    // partial of warp w of CTA r at slot 16 r + w, in both CTAs; every lane sums the 32 slots
+    if (lane == 0) {
+      float* slot = part + buf * 32 + 16 * rank + warp;
+      *slot = v;
+      st_cluster(slot, (uint32_t)(rank ^ 1), v);
+    }
+    cluster_sync();
+    float t = part[buf * 32 + lane];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
     return t;
   };
   // store the row (x, or c x + r when affine) to w1 / multiply m1 by it / w2 (any may be null)
@@ -113,13 +156,14 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
 #pragma unroll
     for (int q = 0; q < QR; ++q) Stg[q * T + tid] = make_float4(x[q][0].x, x[q][0].y, x[q][1].x, x[q][1].y);
     __syncthreads();
-    for (int i = tid; i < N; i += T) {
-      const int t = i / B, o = i - t * B;
+    const int iend = min(C::NP, N - pos0);
+    for (int i = tid; i < iend; i += T) {
+      const int t = i / B, o = i - t * B, g = pos0 + i;
       const float xv = *elem(o >> 2, t, o & 3);
-      const float v = i == tgt ? 0.0f : (affine ? fmaf(c, xv, r) : xv);
-      const size_t ro = (size_t)row * N + i;
+      const float v = g == tgt ? 0.0f : (affine ? fmaf(c, xv, r) : xv);
+      const size_t ro = (size_t)row * N + g;
       if (w1) w1[ro] = v;
-      if (m1) m1[ro] = i == tgt ? 0.0f : m1[ro] * v;
+      if (m1) m1[ro] = g == tgt ? 0.0f : m1[ro] * (v * kProdScale);
       if (w2) w2[ro] = v;
     }
     __syncthreads();
@@ -245,10 +289,11 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   if (DIR == 0 && (pend_slot >= 0 || pend_save))
     store_state(pend_slot >= 0 ? p.store + (size_t)pend_slot * p.state_rows * N : nullptr, nullptr,
                 pend_save ? p.state : nullptr, false, 0.f, 0.f);
-  if (tid == 0 && cta_t < p.t_begin + p.t_count) {
+  if (tid == 0 && rank == 0 && cta_t < p.t_begin + p.t_count) {
     if (p.logs) p.logs[row] = lgs;
     if (p.status && sts) atomicOr(p.status + row, sts);
   }
+  if (CL == 2) cluster_sync();  // no CTA leaves while its peer may still address its shared memory
 }
 
 }  // namespace lsk

@@ -18,6 +18,7 @@ struct PropKernelInfo {
   cudaError_t (*launch)(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s);
   int (*smem_bytes)(int rw2);
   bool (*serves)(int N);
+  int cpt = 1;  // CTAs per target (2: a thread-block cluster of two CTAs shares one target)
 };
 
 void ls_register_prop_kernels(std::vector<PropKernelInfo>& out);

@@ -42,8 +42,25 @@ constexpr int kMaxStore = 64;    // store loci per launch
 // every kAluMod-th quad of a lane's slice takes theta by a bit test and select instead of the table
 // (0: none); half of the quads measured fastest on GB300 (the table loads and the selects then
 // share the load between the shared-memory and integer pipes)
-constexpr int kAluMod = 2;
+#ifndef LS_X_ALUMOD
+#define LS_X_ALUMOD 2
+#endif
+#ifndef LS_X_UNI
+#define LS_X_UNI 1
+#endif
+#ifndef LS_X_NACC
+#define LS_X_NACC 4
+#endif
+#ifndef LS_X_RED4
+#define LS_X_RED4 0
+#endif
+constexpr int kAluMod = LS_X_ALUMOD;
 constexpr float kEps = 2.220446049250313e-16f;  // DBL_EPSILON = 2^-52, exact in FP32 (Eq. distmat)
+// alpha * beta products for the posterior (Eq. postprob) are formed as alpha * (beta * 2^100): the
+// power of two is exact and cancels in the normalisation, and it lifts products that FP32 would
+// flush to zero (rho = 0 leaves the copied donor's alpha and beta each far below the row maxima)
+// while staying below overflow (alpha <= 1 and beta <= N, so the scaled product is < 2^100 N).
+constexpr float kProdScale = 0x1p100f;
 
 struct PropParams {
   const uint32_t* bits2;  // doubled packed rows [L][rw2]: bit b of row l = h[l][b mod N], b < 2N
@@ -192,7 +209,7 @@ struct PropCfg {
   // dynamic shared memory: mbarriers, partial sums, log ring, per-target log scale and status,
   // timeout flag, TMA ring, store/load staging (the emission tables are static shared memory)
   static constexpr int BAR_OFF = 0;
-  static constexpr int PART_OFF = BAR_OFF + kSlots * 8;
+  static constexpr int PART_OFF = ((BAR_OFF + kSlots * 8 + 15) / 16) * 16;  // 16-byte aligned partials
   static constexpr int LOGR_OFF = PART_OFF + 2 * TPW * W * 8;  // two buffers of float2 partials
   static constexpr int LOG_OFF = ((LOGR_OFF + TPW * 32 * 4 + 7) / 8) * 8;
   static constexpr int ST_OFF = LOG_OFF + TPW * 8;
@@ -236,6 +253,12 @@ __host__ __device__ __forceinline__ void slice_of(int sigma, int S, int N, int& 
 template <int DIR, int TPW, int W, int KQ, int PIM, int ST>
 __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_prop_kernel(const PropParams p) {
   static_assert(ST == 0 || (DIR == 0 && PIM == 0), "statistic passes run forward with the uniform prior");
+  // UNI (uniform prior, no statistic): theta = base * f with base = max(1-mu, mu) and f in {1, ratio},
+  // ratio = min(1-mu, mu) / base; a cell is c' x + r' (c' = c base, r' = r base), then multiplied by
+  // ratio where f = ratio -- a predicated multiply on the bit-select quads, f from the table on the
+  // others.  "small" bits (f = ratio) are the mismatches (or the matches when mu > 1/2).
+  constexpr bool UNI = LS_X_UNI && PIM == 0 && ST == 0;
+  constexpr int NACC = UNI ? LS_X_NACC : 2;
   using C = PropCfg<TPW, W, KQ>;
   constexpr int SPW = C::SPW, S = C::S, NWORD = C::NWORD, THREADS = C::THREADS;
   constexpr int step_dir = DIR == 0 ? 1 : -1;
@@ -302,7 +325,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
         if (ok) {
           const float v = diag ? 0.0f : *sp;
           if (w1) w1[ro] = v;
-          if (m1) m1[ro] = diag ? 0.0f : m1[ro] * v;
+          if (m1) m1[ro] = diag ? 0.0f : m1[ro] * (v * kProdScale);
           if (w2) w2[ro] = v;
         }
       } else {
@@ -331,7 +354,13 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   // emission table of step 0 (for scalar mu it serves every step)
   if (tid < 64) {
     const int e = tid >> 2, k = tid & 3;
-    lutf[tid] = ((e >> k) & 1) ? p.thm[p.l_first] : p.thx[p.l_first];
+    if (UNI) {
+      const float a = p.thm[p.l_first], b = p.thx[p.l_first];
+      const float bs = fmaxf(a, b);
+      lutf[tid] = ((e >> k) & 1) ? 1.0f : (bs > 0.0f ? __fdiv_rn(fminf(a, b), bs) : 0.0f);
+    } else {
+      lutf[tid] = ((e >> k) & 1) ? p.thm[p.l_first] : p.thx[p.l_first];
+    }
     if (ST == 2) s_hlut[0][tid] = ((e >> k) & 1) ? 0.0f : (p.eta_vec ? p.eta_vec[p.l_first] : p.eta);
   }
   if (tid < TPW) {
@@ -425,6 +454,13 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     for (int off = TPW; off < 32; off <<= 1) {
       v += __shfl_xor_sync(0xffffffffu, v, off);
       if (ST) u += __shfl_xor_sync(0xffffffffu, u, off);
+    }
+    if (LS_X_RED4 && !ST && W == 4) {  // the W partials of target tl in one 16-byte load
+      if (sl == 0) buf[tl * W + warp] = v;
+      __syncthreads();
+      const float4 e = *reinterpret_cast<const float4*>(buf + tl * W);
+      tu = 0.0f;
+      return (e.x + e.y) + (e.z + e.w);
     }
     float2* b2 = reinterpret_cast<float2*>(buf);
     if (sl == 0) b2[tl * W + warp] = make_float2(v, u);
@@ -559,16 +595,23 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     }
 
     // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
-    const uint32_t inv = ((rw[abit >> 5] >> (abit & 31)) & 1u) ? 0u : 0xffffffffu;  // target allele
+    uint32_t inv = ((rw[abit >> 5] >> (abit & 31)) & 1u) ? 0u : 0xffffffffu;  // target allele
+    // UNI: base, ratio and the sense of the "small" bits of this locus
+    const float u_base = fmaxf(cur_thm, cur_thx);
+    const float u_ratio = u_base > 0.0f ? __fdiv_rn(fminf(cur_thm, cur_thx), u_base) : 0.0f;
+    if (UNI && cur_thm < cur_thx) inv = ~inv;  // mu > 1/2: the matches carry the smaller factor
     // shared address of this step's table (256-byte aligned, so a byte permute can put a nibble
     // offset in its low byte and the load needs no further address arithmetic)
     uint32_t lut_b = lut_base + (p.mu_vec ? (uint32_t)((step & 1) << 8) : 0u);
     // the loads below are plain asm that the compiler may move; deriving their address from a
     // volatile move here keeps them after the previous locus' barrier (which publishes the table)
     asm volatile("mov.b32 %0, %0;" : "+r"(lut_b));
-    const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
+    const float cu = UNI ? c * u_base : c, ru = UNI ? r * u_base : r;
+    const f2 C2 = make_float2(cu, cu), R2 = make_float2(ru, ru);
     const f2 CW2 = make_float2(cw, cw), RW2 = make_float2(rws, rws);
-    f2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    f2 acc[NACC];
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) acc[a] = make_float2(0.f, 0.f);
     f2 accw0 = make_float2(0.f, 0.f), accw1 = make_float2(0.f, 0.f);
     // Software pipeline: the emission-table entries are loaded kLA quads ahead of their use from a
     // rotating register buffer; a slice word's nibbles are prepared when the lookahead enters it.
@@ -619,23 +662,42 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
           const f2 u23 = __ffma2_rn(C2, x[k][1], __fmul2_rn(R2, p23));
           x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
           x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
-          acc0 = __fadd2_rn(acc0, x[k][0]);
-          acc1 = __fadd2_rn(acc1, x[k][1]);
+          acc[0] = __fadd2_rn(acc[0], x[k][0]);
+          acc[1] = __fadd2_rn(acc[1], x[k][1]);
         } else {         // S = sum_j t_j pi_j
           const f2 u01 = __ffma2_rn(C2, x[k][0], R2);
           const f2 u23 = __ffma2_rn(C2, x[k][1], R2);
           x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
           x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
-          acc0 = __ffma2_rn(x[k][0], p01, acc0);
-          acc1 = __ffma2_rn(x[k][1], p23, acc1);
+          acc[0] = __ffma2_rn(x[k][0], p01, acc[0]);
+          acc[1] = __ffma2_rn(x[k][1], p23, acc[1]);
         }
+      } else if (UNI) {
+        const f2 u01 = __ffma2_rn(C2, x[k][0], R2);
+        const f2 u23 = __ffma2_rn(C2, x[k][1], R2);
+        if (sel_quad(k)) {  // multiply the "small" cells by ratio (predicated, no select)
+          const uint32_t w = mw[(k >> 3) & 1];
+          const int b = 4 * (k & 7);
+          float a0 = u01.x, a1 = u01.y, a2 = u23.x, a3 = u23.y;
+          if (!((w >> b) & 1u)) a0 = __fmul_rn(a0, u_ratio);
+          if (!((w >> (b + 1)) & 1u)) a1 = __fmul_rn(a1, u_ratio);
+          if (!((w >> (b + 2)) & 1u)) a2 = __fmul_rn(a2, u_ratio);
+          if (!((w >> (b + 3)) & 1u)) a3 = __fmul_rn(a3, u_ratio);
+          x[k][0] = make_float2(a0, a1);
+          x[k][1] = make_float2(a2, a3);
+        } else {
+          x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
+          x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
+        }
+        acc[(2 * k) % NACC] = __fadd2_rn(acc[(2 * k) % NACC], x[k][0]);
+        acc[(2 * k + 1) % NACC] = __fadd2_rn(acc[(2 * k + 1) % NACC], x[k][1]);
       } else {
         const f2 u01 = __ffma2_rn(C2, x[k][0], R2);
         const f2 u23 = __ffma2_rn(C2, x[k][1], R2);
         x[k][0] = __fmul2_rn(make_float2(t.x, t.y), u01);
         x[k][1] = __fmul2_rn(make_float2(t.z, t.w), u23);
-        acc0 = __fadd2_rn(acc0, x[k][0]);
-        acc1 = __fadd2_rn(acc1, x[k][1]);
+        acc[0] = __fadd2_rn(acc[0], x[k][0]);
+        acc[1] = __fadd2_rn(acc[1], x[k][1]);
         if (ST) {
           const int kw = ST ? k : 0;
           const f2 v01 = __fmul2_rn(make_float2(t.x, t.y), __ffma2_rn(CW2, wv[kw][0], RW2));
@@ -655,7 +717,8 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
         }
       }
     }
-    xs = cur_thx * fmaf(c, xs, r);  // junk cells: theta = mu in every lane
+    // junk cells: theta = mu in every lane (UNI: always the "small" factor, as their bits are 0)
+    xs = UNI ? __fmul_rn(u_ratio, __fmaf_rn(cu, xs, ru)) : cur_thx * fmaf(c, xs, r);
     if (ST) {  // the same operations as a mismatch cell
       const float v = __fmul_rn(cur_thx, __fmaf_rn(cw, ws, rws));
       ws = ST == 2 ? __fmaf_rn(p.eta_vec ? p.eta_vec[l] : p.eta, xs, v) : v;
@@ -673,13 +736,23 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     // emission table of the next locus (mu varying per locus), into the other buffer
     if (p.mu_vec && tid < 64 && step + 1 < p.n_steps) {
       const int e = tid >> 2, k = tid & 3;
-      lutf[((step + 1) & 1) * 64 + tid] = ((e >> k) & 1) ? nx_thm : nx_thx;
+      if (UNI) {
+        const float bs = fmaxf(nx_thm, nx_thx);
+        lutf[((step + 1) & 1) * 64 + tid] = ((e >> k) & 1) ? 1.0f : (bs > 0.0f ? __fdiv_rn(fminf(nx_thm, nx_thx), bs) : 0.0f);
+      } else {
+        lutf[((step + 1) & 1) * 64 + tid] = ((e >> k) & 1) ? nx_thm : nx_thx;
+      }
       if (ST == 2) s_hlut[(step + 1) & 1][tid] = ((e >> k) & 1) ? 0.0f : p.eta_vec[l + 1];
     }
 
     float wtot = 0.0f;
-    const float tot = reduce2((acc0.x + acc0.y) + (acc1.x + acc1.y), (accw0.x + accw0.y) + (accw1.x + accw1.y),
-                              part + (step & 1) * 2 * TPW * W, wtot);
+    // fold the NACC accumulator pairs (a power of two) pairwise, then the last pair
+#pragma unroll
+    for (int h = NACC / 2; h >= 2; h >>= 1)
+#pragma unroll
+      for (int a = 0; a < h; ++a) acc[a] = __fadd2_rn(acc[a], acc[a + h]);
+    const float lsum = (acc[0].x + acc[0].y) + (acc[1].x + acc[1].y);
+    const float tot = reduce2(lsum, (accw0.x + accw0.y) + (accw1.x + accw1.y), part + (step & 1) * 2 * TPW * W, wtot);
     if (ST) wsum_prev = wtot - n_junk * ws;
     float sig = tot - n_junk * xs;
     if (DIR == 1 && !PIM) sig *= p.pi_u;

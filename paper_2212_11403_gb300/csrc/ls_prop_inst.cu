@@ -34,19 +34,36 @@ bool serves_prop(int N) {
   return lsk::PropCfg<TPW, W, KQ>::serves(N);
 }
 
-template <int QS>
+// grid = number of targets; CL CTAs (a thread-block cluster when CL = 2) per target
+template <int QS, int CL>
 cudaError_t launch_hyb(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
-  if (dir == 0) lsk::ls_hyb_kernel<0, QS><<<grid, lsk::kHybThreads, smem, s>>>(p);
-  else lsk::ls_hyb_kernel<1, QS><<<grid, lsk::kHybThreads, smem, s>>>(p);
-  return cudaGetLastError();
+  if (CL == 1) {
+    if (dir == 0) lsk::ls_hyb_kernel<0, QS, 1><<<grid, lsk::kHybThreads, smem, s>>>(p);
+    else lsk::ls_hyb_kernel<1, QS, 1><<<grid, lsk::kHybThreads, smem, s>>>(p);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(CL * grid), 1, 1);
+  cfg.blockDim = dim3(lsk::kHybThreads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (dir == 0) return cudaLaunchKernelEx(&cfg, lsk::ls_hyb_kernel<0, QS, CL>, p);
+  return cudaLaunchKernelEx(&cfg, lsk::ls_hyb_kernel<1, QS, CL>, p);
 }
 template <int QS>
 int smem_hyb(int) {
   return lsk::HybCfg<QS>::smem_bytes();
 }
-template <int QS>
+template <int QS, int CL>
 bool serves_hyb(int N) {
-  return lsk::HybCfg<QS>::serves(N);
+  return lsk::HybCfg<QS>::serves(N, CL);
 }
 
 }  // namespace
@@ -55,8 +72,13 @@ bool serves_hyb(int N) {
 // shared memory
 #define LS_REGH(QS)                                                                                 \
   out.push_back(PropKernelInfo{1, lsk::kHybThreads / 32, lsk::kHybQR + QS, 0, 0,                    \
-                               {(const void*)lsk::ls_hyb_kernel<0, QS>, (const void*)lsk::ls_hyb_kernel<1, QS>}, \
-                               launch_hyb<QS>, smem_hyb<QS>, serves_hyb<QS>})
+                               {(const void*)lsk::ls_hyb_kernel<0, QS, 1>, (const void*)lsk::ls_hyb_kernel<1, QS, 1>}, \
+                               launch_hyb<QS, 1>, smem_hyb<QS>, serves_hyb<QS, 1>})
+// a cluster of two CTAs (on two SMs) per target: N in (57344, 2 x 2048 (12 + QS)]
+#define LS_REGH2(QS)                                                                                \
+  out.push_back(PropKernelInfo{1, lsk::kHybThreads / 32, lsk::kHybQR + QS, 0, 0,                    \
+                               {(const void*)lsk::ls_hyb_kernel<0, QS, 2>, (const void*)lsk::ls_hyb_kernel<1, QS, 2>}, \
+                               launch_hyb<QS, 2>, smem_hyb<QS>, serves_hyb<QS, 2>, 2})
 
 #define LS_REGP(T, Wp, K, P)                                                                        \
   out.push_back(PropKernelInfo{T, Wp, K, P, 0,                                                      \
@@ -127,9 +149,18 @@ void ls_register_group7(std::vector<PropKernelInfo>& out) {
   LS_REGP(8, 4, 16, 1);
 }
 #elif LS_INST_GROUP == 10
-void ls_register_group10(std::vector<PropKernelInfo>&) {}
+void ls_register_group10(std::vector<PropKernelInfo>& out) {
+  // two-CTA clusters: N in (57344, 81920]
+  LS_REGH2(4);
+  LS_REGH2(8);
+}
 #elif LS_INST_GROUP == 11
-void ls_register_group11(std::vector<PropKernelInfo>&) {}
+void ls_register_group11(std::vector<PropKernelInfo>& out) {
+  // N in (81920, 114688]
+  LS_REGH2(12);
+  LS_REGH2(13);
+  LS_REGH2(16);
+}
 #elif LS_INST_GROUP == 12
 void ls_register_group12(std::vector<PropKernelInfo>& out) {
   // register + shared-memory state, N in (20480, 40960]

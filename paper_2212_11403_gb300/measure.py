@@ -3,6 +3,7 @@
     python -m paper_2212_11403_gb300.measure prior   # N=20000, L=50000, Gamma(2,1) prior matrix, checkpoints
     python -m paper_2212_11403_gb300.measure grad    # N=L=10000, gradient over 100 rho intervals
     python -m paper_2212_11403_gb300.measure sparse  # learned sparse path against dense (N=20000) and at N=50000
+    python -m paper_2212_11403_gb300.measure table   # ls_forward throughput against Delta-l (N=10000, N=100000)
 
 CUDA events around each call on the current stream, after one warm-up call; inputs resident in
 device memory.  These are measurements of the library only; the accuracy of each path against the
@@ -172,10 +173,67 @@ def measure_sparse_case(N, L, K=512):
                  seconds=t)]
 
 
+def measure_table(big_L=10000):
+    """The paper's single-step table API at scale (Sec. 5, the Delta-L figures): ls_forward of a
+    table over all N targets by Delta-l loci, throughput N^2 Delta-l / t, at N = 10000 (L = 10000)
+    for Delta-l from 1 to 9999; then one forward of a 100000 x 100000 table over big_L loci."""
+    import torch
+    out = []
+    w = synth.make_workload("ls_n10000_l10000")
+    N, L = w["N"], w["L"]
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        fw = ls.ls_table_create(ctx, ls.LS_FWD, 0, N)
+        for dl in (1, 2, 4, 16, 64, 256, 1024, 4096, L - 1):
+            def run():
+                ls.ls_table_reset(fw)
+                ls.ls_forward(ctx, fw, 0)       # initialise at locus 0 (outside the timed call)
+            run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ls.ls_forward(ctx, fw, dl)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            cells = float(N) * N * dl
+            out.append(dict(workload="ls_n10000_l10000", path="ls_forward over Delta-l loci, table of all targets",
+                            N=N, delta_l=dl, seconds=t, cell_updates_per_s=cells / t,
+                            frac_fp32=4 * cells / t / P_FP32))
+        ls.ls_table_destroy(fw)
+    finally:
+        ls.ls_destroy(ctx)
+    N = 100000
+    w = synth.make_workload("ls_n50000_l20000", N=N, L=big_L, seed=7100, founders=N // 25)
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        fw = ls.ls_table_create(ctx, ls.LS_FWD, 0, N)
+        for dl in (1, 16, 256, big_L - 1):
+            ls.ls_table_reset(fw)
+            ls.ls_forward(ctx, fw, 0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ls.ls_forward(ctx, fw, dl)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            cells = float(N) * N * dl
+            out.append(dict(workload="ls_n50000_l20000 generator at N=100000, L=%d" % big_L,
+                            path="ls_forward over Delta-l loci, 100000 x 100000 FP32 table (40 GB)", N=N,
+                            delta_l=dl, seconds=t, cell_updates_per_s=cells / t, frac_fp32=4 * cells / t / P_FP32))
+        ls.ls_table_destroy(fw)
+    finally:
+        ls.ls_destroy(ctx)
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["prior", "grad", "sparse", "sparse_case"])
+    ap.add_argument("what", choices=["prior", "grad", "sparse", "sparse_case", "table"])
     ap.add_argument("--N", type=int, default=20000, help="sparse_case: haplotypes")
     ap.add_argument("--L", type=int, default=2000, help="sparse_case: loci")
     a = ap.parse_args()
@@ -183,7 +241,7 @@ def main():
     if a.what == "sparse_case":
         recs = measure_sparse_case(a.N, a.L)
     else:
-        recs = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse)[a.what]()
+        recs = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse, table=measure_table)[a.what]()
     for rec in recs:
         print(json.dumps(rec), flush=True)
 

@@ -194,3 +194,33 @@ def test_pac_grad_n10000_l10000_sampled_targets(ls):
     for k in (3, 71):
         fd = (pac_at(k=k, d=h) - pac_at(k=k, d=-h)) / (2 * h)
         assert abs(gr[k] - fd) <= G_RTOL * (abs(fd) + cr[k]) + fd_tol, (k, gr[k], fd)
+
+
+def test_pac_grad_in_target_blocks_matches_one_block(ls):
+    """the gradient's scratch ceiling (LS_GRAD_BUDGET_MB) splits the targets into blocks: with a
+    ceiling that forces blocks of 13 targets the result matches the single-block run (each target's
+    FP32 recursions may run in another launch configuration, so the sums agree to the gradient
+    tolerance, not bit for bit) and the oracle."""
+    import os
+    N, L, K = 517, 200, 100
+    w = synth.make_workload("ls_n10000_l10000", N=N, L=L, seed=77)
+    iv = synth.rho_intervals(L, K)
+    ctx = ls.ls_create(w["h"])
+    try:
+        ls.ls_set_params(ctx, w["rho"], w["mu"])
+        rc0, pac0, gm0, gr0 = ls.ls_pac_grad(ctx, iv, K)
+        os.environ["LS_GRAD_BUDGET_MB"] = "8"   # (3 x 100 + 2) x 517 x 4 bytes = 0.62 MB per target
+        try:
+            rc1, pac1, gm1, gr1 = ls.ls_pac_grad(ctx, iv, K)
+        finally:
+            del os.environ["LS_GRAD_BUDGET_MB"]
+    finally:
+        ls.ls_destroy(ctx)
+    assert rc0 == rc1 == 0
+    ref = oracle.pac_grad(w["h"], w["rho"], w["mu"], iv, K)
+    check_grad(pac0, gm0, gr0, ref, w["rho"], w["mu"], L, iv, K, N, N)
+    check_grad(pac1, gm1, gr1, ref, w["rho"], w["mu"], L, iv, K, N, N)
+    cr, cm = magnitudes(w["rho"], w["mu"], L, iv, K, N)
+    assert abs(pac1 - pac0) <= 1e-9 * abs(pac0)
+    assert abs(gm1 - gm0) <= 1e-6 * (abs(gm0) + cm)
+    assert np.all(np.abs(gr1 - gr0) <= 1e-6 * (np.abs(gr0) + cr))
