@@ -126,6 +126,40 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ls_prop_kernel_dram_n5000.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2212_11403_gb300", "csrc", f) for f in ("ls_prop.cuh", "ls_prop_inst.cu")]
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(N, L, D):
+    """DRAM bytes per step of the propagation launches from the committed ncu summary: the captured
+    bytes (same N and D, fewer loci) plus the extra packed-row reads of the longer run, or None when
+    the summary was taken on other kernel sources or another workload shape."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha256_16") != kernel_digest():
+            return None
+        if int(kv["N"]) != N or int(kv["D"]) != D:
+            return None
+        rows = float(kv["row_bytes_per_locus_per_pass"]) * 2 * (L - int(kv["L"]))
+        return float(kv["dram_bytes_per_step"]) + rows
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -255,8 +289,11 @@ def main():
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     p_fp32 = 2 * 128 * nsm * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     achieved = 8.0 * cells / (t_prop / 1e3) / 1e12
+    traffic = dram_traffic(N, L, D)
     roof = dict(bound="alu", kernel="ls_prop_kernel (forward + backward launches)", achieved=achieved, peak=p_fp32,
-                unit="TFLOP/s", frac=achieved / p_fp32, traffic=None,
+                unit="TFLOP/s", frac=achieved / p_fp32, traffic=traffic,
+                traffic_unit="DRAM bytes per step (ncu, profiles/ls_prop_kernel_dram_n5000.txt)",
+                algorithmic_bytes=3.0 * 4 * D * float(N) * N,
                 peak_basis="FP32 pipe 2 x 128 lanes x %d SMs x %.0f MHz (max SM clock, MEASURED_PEAKS.json)" % (nsm, sm_max),
                 phase_ms={"forward": float(ph[0]), "backward": float(ph[1]), "decode": float(ph[2]),
                           "symmetrise": float(ph[3])})

@@ -284,16 +284,25 @@ int ls_propose(ls_ctx* ctx, int32_t C, int32_t K, const ls_mlp* mlp, int32_t* id
  * longer); (lookahead + 1) K <= 1536.  With pool = 1 the donors outside the set are carried as one
  * aggregate state with their average emission (allele counts of the locus minus the set's
  * matches), so the normalisers include their mass as in the dense chain; leaving donors' mass
- * joins it and entering donors start from its average.  d_out
- * device float [D][N][N]: d_ij of Eq. distmat where j is in i's set and i in j's set at that
- * locus' window, NaN elsewhere ("uncovered"), 0 on the diagonal.  Targets whose largest forward
- * mass on donors leaving their set exceeds lost_tol (lost_tol < 0: never) get dense rows
- * (requires N within the dense kernels' range); *n_fallback_out receives their number.
- * lost_out device float [N] (may be NULL) receives that mass per target; pac_out the
- * log-likelihood of the restricted chains.  Synchronous.  Uniform prior only. */
+ * joins it and entering donors start from its average.  The posterior at a decode locus is the
+ * pooled chain's: normalised over the set and the pool state, every outside donor receiving an
+ * equal share of the pool's posterior.
+ * d_out device float [D][N][N], complete with pool = 1: d_ij of Eq. distmat from the two targets'
+ * posteriors, where an outside donor's posterior is that estimated share; 0 on the diagonal.  With
+ * pool = 0 entries with an outside donor on either side are NaN.  Targets whose largest forward
+ * mass on donors leaving their set exceeds lost_tol (lost_tol < 0: never) get dense rows (requires
+ * N within the dense kernels' range); *n_fallback_out receives their number.
+ * trust_out (device uint32 [D][N][ceil(N/32)], may be NULL): bit j % 32 of word j / 32 of row i is 1
+ * where d_ij needs no estimate and is within the error budget: both halves come from chain
+ * posteriors (j in i's set and i in j's set, or dense rows) and either both targets have dense rows
+ * or d_ij <= d_trust.  lost_out device float [N] (may be NULL) receives the lost mass per target;
+ * pout_out device float [D][N] (may be NULL) the pooled chain's posterior mass on all outside donors
+ * per decode locus and target (0 without a pool; fallback targets keep their sparse value);
+ * pac_out the log-likelihood of the restricted chains.  Synchronous.  Uniform prior only. */
 int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, int32_t lookahead, int32_t pool,
                       const int32_t* decode_loci, int32_t D, float* d_out, float lost_tol, float* lost_out,
-                      double* pac_out, uint32_t* status_out, int32_t* n_fallback_out, ls_stream_t stream);
+                      double* pac_out, uint32_t* status_out, int32_t* n_fallback_out, float d_trust,
+                      uint32_t* trust_out, float* pout_out, ls_stream_t stream);
 
 /* ---- fused pipeline without allocation --------------------------------------------------- */
 

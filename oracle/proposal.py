@@ -141,11 +141,17 @@ def lookahead_sets(S, span=1):
 def sparse_posteriors(h, rho, mu, sets, ws, loci, pool=False):
     """Posteriors [N, len(loci), N] of the chains restricted to per-window donor sets (sets
     [N, Wn, K], ascending, -1 padded), prior 1/(N-1) kept, continuation only for donors in the sets
-    of both loci; 0 outside the set.  pool=False drops the recombination mass that goes to donors
-    outside the set.  pool=True carries those donors as one aggregate state o with their average
-    emission at each locus (count of outside donors sharing the target's allele), o <- theta_out c o
+    of both loci.
+
+    pool=False drops the recombination mass that goes to donors outside the set; posteriors are
+    normalised over the set and are 0 outside it.
+
+    pool=True carries the outside donors as one aggregate state o with their average emission at
+    each locus (count of outside donors sharing the target's allele), o <- theta_out c o
     + r sum_out theta, adds o to the normalisers, moves the mass of leaving donors into o and starts
-    entering donors at o's average."""
+    entering donors at o's average.  The posterior is that of the pooled chain over its states (the
+    set's donors and the pool): the normaliser adds the pool's forward mass times its donors' mean
+    backward value, and every outside donor receives an equal share of the pool's posterior mass."""
     L, N = h.shape
     pi = 1.0 / (N - 1)
     mu = np.broadcast_to(np.asarray(mu, dtype=np.float64), (L,))
@@ -178,12 +184,14 @@ def sparse_posteriors(h, rho, mu, sets, ws, loci, pool=False):
     for i in range(N):
         setof = [[int(j) for j in sets[i, l // ws] if j >= 0] for l in range(L)]
         alpha = [None] * L
+        apool = [0.0] * L   # forward pool mass at each locus (pool=True)
         # forward
         a = {j: theta(0, i, j) * pi for j in setof[0]}
         ts, no = out_sum(0, i, setof[0])
         o = pi * ts if pool else 0.0
         tot = sum(a.values()) + o
         alpha[0] = a
+        apool[0] = o
         for l in range(1, L):
             if setof[l] != setof[l - 1]:
                 a, o = move(a, setof[l - 1], setof[l], o)
@@ -194,6 +202,7 @@ def sparse_posteriors(h, rho, mu, sets, ws, loci, pool=False):
                 o = (ts / no if no > 0 else 0.0) * (c * o) + r * ts
             tot = sum(a.values()) + o
             alpha[l] = a
+            apool[l] = o
         # backward (t = theta beta)
         t = {j: theta(L - 1, i, j) for j in setof[L - 1]}
         beta = {j: 1.0 for j in setof[L - 1]}
@@ -201,18 +210,28 @@ def sparse_posteriors(h, rho, mu, sets, ws, loci, pool=False):
         o = ts if pool else 0.0
         tot = sum(t.values()) + o
         for l in range(L - 1, -1, -1):
+            nout = N - 1 - len(setof[l])
+            bpool = 1.0   # mean backward value of the outside donors at l
             if l < L - 1:
                 if setof[l] != setof[l + 1]:
                     t, o = move(t, setof[l + 1], setof[l], o)
                 c, r = (1 - rho[l]) / (pi * tot), rho[l]
                 beta = {j: c * t[j] + r for j in setof[l]}
+                bpool = c * (o / nout if nout > 0 else 0.0) + r
                 t = {j: theta(l, i, j) * beta[j] for j in setof[l]}
                 if pool:
                     ts, no = out_sum(l, i, setof[l])
                     o = (ts / no if no > 0 else 0.0) * (c * o) + r * ts
                 tot = sum(t.values()) + o
             if l in slot:
-                z = sum(alpha[l][j] * beta[j] for j in setof[l])
+                zp = apool[l] * bpool if (pool and nout > 0) else 0.0
+                z = sum(alpha[l][j] * beta[j] for j in setof[l]) + zp
                 for j in setof[l]:
                     out[i, slot[l], j] = alpha[l][j] * beta[j] / z
+                if pool and nout > 0:
+                    share = zp / (z * nout)
+                    inset = set(setof[l])
+                    for j in range(N):
+                        if j != i and j not in inset:
+                            out[i, slot[l], j] = share
     return out

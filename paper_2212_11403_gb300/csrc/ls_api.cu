@@ -1264,7 +1264,8 @@ extern "C" {
 
 int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, int32_t lookahead, int32_t pool,
                       const int32_t* decode_loci, int32_t D, float* d_out, float lost_tol, float* lost_out,
-                      double* pac_out, uint32_t* status_out, int32_t* n_fallback_out, ls_stream_t stream) {
+                      double* pac_out, uint32_t* status_out, int32_t* n_fallback_out, float d_trust,
+                      uint32_t* trust_out, float* pout_out, ls_stream_t stream) {
   int rc = check_ctx(ctx);
   if (rc) return rc;
   if (!ctx->have_params) return fail(LS_ERR_STATE, "parameters not set");
@@ -1281,16 +1282,21 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
     if (k && decode_loci[k] <= decode_loci[k - 1]) return fail(LS_ERR_ARG, "decode loci must be strictly increasing");
   }
   if (!is_device_ptr(idx) || !is_device_ptr(d_out)) return fail(LS_ERR_ARG, "idx and d_out must be device memory");
+  if (trust_out && !is_device_ptr(trust_out)) return fail(LS_ERR_ARG, "trust_out must be device memory");
+  if (pout_out && !is_device_ptr(pout_out)) return fail(LS_ERR_ARG, "pout_out must be device memory");
   const int Wn = (L + WS - 1) / WS;
   cudaStream_t s = (cudaStream_t)stream;
   DevBufs db;
-  float *P, *lost;
+  float *P, *lost, *poolf = nullptr, *share = nullptr;
   double* logs;
   uint32_t* stat;
   int* wos;
+  uint8_t* dense_row;
   if ((rc = db.get(&P, (size_t)D * N * K)) || (rc = db.get(&lost, N)) || (rc = db.get(&logs, N)) ||
-      (rc = db.get(&stat, N)) || (rc = db.get(&wos, D)))
+      (rc = db.get(&stat, N)) || (rc = db.get(&wos, D)) || (rc = db.get(&dense_row, N)) ||
+      (pool && ((rc = db.get(&poolf, (size_t)D * N)) || (rc = db.get(&share, (size_t)D * N)))))
     return rc;
+  CUDA_TRY(cudaMemsetAsync(dense_row, 0, N, s));
   const int32_t* sets = idx;
   if (lookahead) {  // run window w on S^w u S^{w+1} (and S^{w-1} with lookahead 2)
     int32_t* U;
@@ -1336,6 +1342,9 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
   }
   sp.logs = logs;
   sp.lost = lost;
+  sp.poolf = poolf;
+  sp.share = share;
+  sp.pout = pout_out;
   if (pool) {  // per-locus allele counts for the outside pool
     int32_t* n1;
     if ((rc = db.get(&n1, L))) return rc;
@@ -1354,9 +1363,8 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
   sp.lost = nullptr;
   e = ls_launch_sparse(1, sp, s);
   if (e != cudaSuccess) return fail(LS_ERR_CUDA, "sparse backward launch: %s", cudaGetErrorString(e));
-  // half distances of the covered entries; NaN (all bits set) elsewhere
-  CUDA_TRY(cudaMemsetAsync(d_out, 0xff, sizeof(float) * (size_t)D * N * N, s));
-  e = ls_launch_sparse_hdist(P, sets, N, K, Wn, wos, D, d_out, s);
+  // half distances: the set's donors from the chains, the others the pool's share (negated) or NaN
+  e = ls_launch_sparse_hdist(P, sets, N, K, Wn, wos, share, D, d_out, s);
   if (e != cudaSuccess) return fail(LS_ERR_CUDA, "sparse distance launch: %s", cudaGetErrorString(e));
   std::vector<float> lh(N);
   CUDA_TRY(cudaMemcpyAsync(lh.data(), lost, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
@@ -1403,10 +1411,13 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
     if ((rc = run_list(ctx, p, tl, nf, s))) return rc;
     e = ls_launch_dense_rows_hdist(prod, nf, N, tl, D, d_out, s);
     if (e != cudaSuccess) return fail(LS_ERR_CUDA, "fallback distance launch: %s", cudaGetErrorString(e));
+    std::vector<uint8_t> flag(N, 0);
+    for (int t : fb) flag[t] = 1;
+    CUDA_TRY(cudaMemcpyAsync(dense_row, flag.data(), N, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // the host flags are copied before they go out of scope
   }
-  const int nt = (N + 31) / 32;
-  lsk::symmetrize_kernel<<<dim3(nt, nt, D), dim3(32, 8), 0, s>>>(d_out, N);
-  CUDA_TRY(cudaGetLastError());
+  e = ls_launch_symmetrize_trust(d_out, N, D, dense_row, d_trust, trust_out, s);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, "symmetrisation launch: %s", cudaGetErrorString(e));
   if (status_out) CUDA_TRY(cudaMemcpyAsync(status_out, stat, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
   std::vector<double> lf(N);
   std::vector<uint32_t> sh(N);

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     __syncthreads();
   }
   double lgs = (tid == 0 && p.logs && !p.init) ? p.logs[row] : 0.0;
+  float lsum = 0.0f, lerr = 0.0f;  // logs of the normalisers since the last fold into lgs
   uint32_t sts = 0u;
   int store_next = 0;
   int next_store_l = p.n_store > 0 ? p.store_loci[0] : -1;
@@ -282,7 +283,18 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
       const float sg = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
       if (sg < 1.17549435e-38f) sts |= 1u;      // LS_STATUS_UNDERFLOW
       if (!(sg <= 3.40282347e+38f)) sts |= 2u;  // LS_STATUS_OVERFLOW
-      lgs += (double)logf(sg);
+      // FP32 sum with an exact error term per addition (two-sum), taken into the FP64 log scale
+      // every 32 loci
+      const float lv = logf(sg);
+      const float s2 = __fadd_rn(lsum, lv);
+      const float bb = __fsub_rn(s2, lsum);
+      lerr = __fadd_rn(lerr, __fadd_rn(__fsub_rn(lsum, __fsub_rn(s2, bb)), __fsub_rn(lv, bb)));
+      lsum = s2;
+      if ((step & 31) == 31 || step == p.n_steps - 1) {
+        lgs += (double)lsum + (double)lerr;
+        lsum = 0.0f;
+        lerr = 0.0f;
+      }
     }
     sig_prev = sig;
   }

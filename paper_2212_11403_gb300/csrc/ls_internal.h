@@ -36,7 +36,9 @@ cudaError_t ls_launch_row_ones(const uint32_t* bits, int row_words, int N, int L
 cudaError_t ls_launch_hapmajor(const uint32_t* bits, int row_words, int N, int L, uint32_t* hw, cudaStream_t s);
 cudaError_t ls_launch_lookahead(const int32_t* idx, int N, int Wn, int K, int span, int32_t* U, cudaStream_t s);
 cudaError_t ls_launch_sparse_hdist(const float* P, const int32_t* idx, int N, int K, int Wn, const int* win_of_slot,
-                                   int D, float* h, cudaStream_t s);
+                                   const float* share, int D, float* h, cudaStream_t s);
+cudaError_t ls_launch_symmetrize_trust(float* d, int N, int D, const uint8_t* dense_row, float d_trust, uint32_t* mask,
+                                       cudaStream_t s);
 cudaError_t ls_launch_dense_rows_hdist(const float* prod, int nf, int N, const int* tlist, int D, float* h,
                                        cudaStream_t s);
 

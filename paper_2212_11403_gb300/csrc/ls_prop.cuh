@@ -479,22 +479,34 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     float dummy;
     return reduce2(v, 0.0f, buf, dummy);
   };
-  // fold the log ring into the FP64 log scales (warp 0; entries 0..cnt-1) and check the normalisers
+  // fold the log ring into the FP64 log scales and check the normalisers (entries 0..cnt-1).  The
+  // ring of target t is written and folded by warp t % W, so the warps share the work and no CTA
+  // barrier is needed; the 32 logs are summed in FP32 with an exact error term per addition
+  // (two-sum), and one FP64 addition per target takes the compensated sum into the log scale.
   auto flush_logs = [&](int cnt) {
-    if (warp != 0) return;
     __syncwarp();
 #pragma unroll
-    for (int t = 0; t < TPW; ++t) {
+    for (int k = 0; k < (TPW + W - 1) / W; ++k) {
+      const int t = warp + k * W;
+      if (t >= TPW) break;
       const float sg = lane < cnt ? lgr[t * 32 + lane] : 1.0f;
       uint32_t stb = 0u;
       if (sg < 1.17549435e-38f) stb |= 1u;      // LS_STATUS_UNDERFLOW: zero or subnormal normaliser
       if (!(sg <= 3.40282347e+38f)) stb |= 2u;  // LS_STATUS_OVERFLOW: infinite or NaN normaliser
-      double v = (double)logf(sg);
+      float v = logf(sg), e = 0.0f;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      for (int off = 16; off > 0; off >>= 1) {
+        const float vo = __shfl_xor_sync(0xffffffffu, v, off);
+        const float eo = __shfl_xor_sync(0xffffffffu, e, off);
+        const float s2 = __fadd_rn(v, vo);
+        const float bb = __fsub_rn(s2, v);
+        const float er = __fadd_rn(__fsub_rn(v, __fsub_rn(s2, bb)), __fsub_rn(vo, bb));  // v + vo - s2, exactly
+        v = s2;
+        e = __fadd_rn(__fadd_rn(e, eo), er);
+      }
       const uint32_t any = __reduce_or_sync(0xffffffffu, stb);
       if (lane == 0) {
-        lgs[t] += v;
+        lgs[t] += (double)v + (double)e;
         sts[t] |= any;
       }
     }
@@ -524,6 +536,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       nx_rr = p.rr[li];
     }
   }
+  // UNI: base and ratio of the emission values (recomputed per locus only with a per-locus mu)
+  float u_base = fmaxf(nx_thm, nx_thx);
+  float u_ratio = u_base > 0.0f ? __fdiv_rn(fminf(nx_thm, nx_thx), u_base) : 0.0f;
   int store_next = 0;
   int next_store_l = p.n_store > 0 ? p.store_loci[0] : -1;  // next locus with a store (-1: none)
   int pend_slot = -1;     // forward: store slot of the previous locus' alpha, written next step
@@ -538,8 +553,10 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       const int li = DIR == 0 ? ln - 1 : ln;
       nx_omr = p.omr[li];
       nx_rr = p.rr[li];
-      nx_thx = p.thx[ln];
-      nx_thm = p.thm[ln];
+      if (!UNI || p.mu_vec) {  // the emission values change between loci only with a per-locus mu
+        nx_thx = p.thx[ln];
+        nx_thm = p.thm[ln];
+      }
     }
     const int j = step & (kRB - 1);
     if (j == 0) {
@@ -597,8 +614,10 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
     uint32_t inv = ((rw[abit >> 5] >> (abit & 31)) & 1u) ? 0u : 0xffffffffu;  // target allele
     // UNI: base, ratio and the sense of the "small" bits of this locus
-    const float u_base = fmaxf(cur_thm, cur_thx);
-    const float u_ratio = u_base > 0.0f ? __fdiv_rn(fminf(cur_thm, cur_thx), u_base) : 0.0f;
+    if (UNI && p.mu_vec) {
+      u_base = fmaxf(cur_thm, cur_thx);
+      u_ratio = u_base > 0.0f ? __fdiv_rn(fminf(cur_thm, cur_thx), u_base) : 0.0f;
+    }
     if (UNI && cur_thm < cur_thx) inv = ~inv;  // mu > 1/2: the matches carry the smaller factor
     // shared address of this step's table (256-byte aligned, so a byte permute can put a nibble
     // offset in its low byte and the load needs no further address arithmetic)
@@ -756,7 +775,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     if (ST) wsum_prev = wtot - n_junk * ws;
     float sig = tot - n_junk * xs;
     if (DIR == 1 && !PIM) sig *= p.pi_u;
-    if (tid < TPW) lgr[tid * 32 + (step & 31)] = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
+    if (lane < TPW && lane % W == warp) lgr[lane * 32 + (step & 31)] = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
     if ((step & 31) == 31 || step == p.n_steps - 1) flush_logs((step & 31) + 1);
     sig_prev = sig;
   }
@@ -768,6 +787,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       store_tile((pend_slot >= 0 && p.wstore) ? p.wstore + (size_t)pend_slot * p.state_rows * N : nullptr, nullptr,
                  pend_save ? p.wstate : nullptr, false, 0.f, 0.f, true);
   }
+  __syncthreads();  // the log scales and status words were last written by other warps
   if (tid < TPW && cta_t + tid < t_end) {
     const int row = row0 + tid;
     const uint32_t stb = sts[tid] | (*flag ? 4u : 0u);  // 4 = LS_STATUS_TIMEOUT

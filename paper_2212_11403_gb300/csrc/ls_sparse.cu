@@ -35,8 +35,15 @@ cudaError_t ls_launch_lookahead(const int32_t* idx, int N, int Wn, int K, int sp
 }
 
 cudaError_t ls_launch_sparse_hdist(const float* P, const int32_t* idx, int N, int K, int Wn, const int* win_of_slot,
-                                   int D, float* h, cudaStream_t s) {
-  lsk::sparse_hdist_kernel<<<dim3(N, D), 256, 0, s>>>(P, idx, N, K, Wn, win_of_slot, h);
+                                   const float* share, int D, float* h, cudaStream_t s) {
+  lsk::sparse_hdist_kernel<<<dim3(N, D), 256, 0, s>>>(P, idx, N, K, Wn, win_of_slot, share, h);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_launch_symmetrize_trust(float* d, int N, int D, const uint8_t* dense_row, float d_trust, uint32_t* mask,
+                                       cudaStream_t s) {
+  const int nt = (N + 31) / 32;
+  lsk::symmetrize_trust_kernel<<<dim3(nt, nt, D), dim3(32, 8), 0, s>>>(d, N, dense_row, d_trust, mask, nt);
   return cudaGetLastError();
 }
 

@@ -18,8 +18,10 @@
 // outside donors at each locus (from the locus' allele count minus the set's own matches):
 //   o <- theta_out (c o) + r sum_{j out} theta_j,   theta_out = sum_{j out} theta_j / |out|,
 // and the normalisers become set sum + o, as in the dense chain.  At a window change the mass of
-// donors leaving the set joins the pool and each entering donor takes the pool's average.  Only
-// the posterior mass on outside donors is then missing from the restricted chain.
+// donors leaving the set joins the pool and each entering donor takes the pool's average.  The
+// posterior is the pooled chain's own: its normaliser adds the pool's forward mass times the mean
+// backward value of the outside donors, and each outside donor receives an equal share of the
+// pool's posterior mass (an estimate, reported apart from the set donors' values).
 //
 // One warp per target, slot s of lane q <-> set index 32 s + q (coalesced set loads and stores);
 // eight targets per CTA share the packed locus rows, staged up to eight rows at a time in shared
@@ -59,7 +61,14 @@ struct SparseParams {
   uint32_t* status;      // [N] status bits (may be null)
   const int32_t* n1;     // [L] haplotypes carrying allele 1 at each locus (outside pool only)
   int pool;              // 1: carry the donors outside the set as one pooled state (below)
+  float* poolf;          // [slots][N] forward: the pool's mass at the store loci (pool = 1)
+  float* share;          // [slots][N] backward: posterior of one outside donor (pool = 1)
+  float* pout;           // [slots][N] backward: posterior mass of all outside donors (may be null)
 };
+
+// posterior products alpha * (beta * 2^100): exact scaling that cancels in the normalisation and
+// keeps products of small alpha and beta above FP32's underflow
+constexpr float kSparseProdScale = 0x1p100f;
 
 // two buffers of per-locus constants and the per-warp set copies used at window changes
 __host__ __device__ inline int sparse_smem_bytes(int ks) {
@@ -244,21 +253,29 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
       const bool is_store = store_next < p.n_store && p.store_loci[store_next] == l;
       float* srow = is_store ? p.store + ((size_t)p.store_slot[store_next] * N + i) * K : nullptr;
       if (DIR == 1 && is_store) {
-        // posterior over the set: alpha (stored by the forward) times beta = c t + r, normalised
+        // posterior: alpha (stored by the forward) times beta = c t + r over the set, plus (pool) the
+        // pool's forward mass times the outside donors' mean backward value c (o / n_out) + r
+        constexpr float S = kSparseProdScale;
         float zb = 0.0f;
 #pragma unroll
         for (int q = 0; q < KS; ++q) {
           const int sq = 32 * q + lane;
-          if (sq < K && id[q] >= 0) zb += srow[sq] * fmaf(c, x[q], r);
+          if (sq < K && id[q] >= 0) zb += srow[sq] * (fmaf(c, x[q], r) * S);
         }
         zb = warp_sum(zb);
-        const float inv = zb > 0.0f ? 1.0f / zb : 0.0f;
+        const int nout = N - 1 - nset;
+        const size_t so = (size_t)p.store_slot[store_next] * N + i;
+        const float zp = (p.pool && nout > 0) ? p.poolf[so] * (fmaf(c, opool / (float)nout, r) * S) : 0.0f;
+        const float z = zb + zp;
+        const float inv = z > 0.0f ? 1.0f / z : 0.0f;
 #pragma unroll
         for (int q = 0; q < KS; ++q) {
           const int sq = 32 * q + lane;
           if (active && sq < K)
-            srow[sq] = id[q] < 0 ? 0.0f : (zb > 0.0f ? srow[sq] * fmaf(c, x[q], r) * inv : eps);
+            srow[sq] = id[q] < 0 ? 0.0f : (z > 0.0f ? srow[sq] * (fmaf(c, x[q], r) * S) * inv : eps);
         }
+        if (p.pool && active && lane == 0) p.share[so] = (nout > 0 && z > 0.0f) ? zp * inv / (float)nout : 0.0f;
+        if (p.pout && active && lane == 0) p.pout[so] = z > 0.0f ? zp * inv : 0.0f;
       }
       float s = 0.0f;
       int nmatch = 0;  // set entries matching the target's allele
@@ -290,6 +307,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
             const int sq = 32 * q + lane;
             if (active && sq < K) srow[sq] = id[q] >= 0 ? x[q] : 0.0f;
           }
+          if (p.pool && active && lane == 0) p.poolf[(size_t)p.store_slot[store_next] * N + i] = opool;
         }
         ++store_next;
       }
@@ -306,19 +324,65 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
   }
 }
 
-// Half distances -log(max(p, eps))/2 of the sparse posteriors, scattered into dense [D][N][N]
-// rows that hold NaN wherever a donor was not in the set.  grid (N, D), 256 threads.
+// Half distances -log(max(p, eps))/2 of the sparse posteriors into dense [D][N][N] rows.  Every
+// entry of row i is first set to the outside donors' estimate: the half distance of the pool's
+// share (share != null), stored NEGATED so that it stays distinguishable (its sign bit, -0.0
+// included), or NaN without a pool; then the set's donors get their own half distances (>= 0).
+// grid (N, D), 256 threads.
 __global__ void sparse_hdist_kernel(const float* __restrict__ P, const int32_t* __restrict__ idx, int N, int K, int Wn,
-                                    const int* __restrict__ win_of_slot, float* __restrict__ h) {
+                                    const int* __restrict__ win_of_slot, const float* __restrict__ share,
+                                    float* __restrict__ h) {
   constexpr float eps = 2.220446049250313e-16f;
   const int i = blockIdx.x, k = blockIdx.y;
   const int w = win_of_slot[k];
   const int32_t* ids = idx + ((size_t)i * Wn + w) * K;
   const float* pr = P + ((size_t)k * N + i) * K;
   float* hr = h + ((size_t)k * N + i) * N;
+  // -log(p)/2 >= 0 for p <= 1: computed as |log(p)/2| so that p = 1 gives +0.0 (chain values keep
+  // the sign bit clear); estimates are stored as -|log(share)/2| (sign bit set, -0.0 included)
+  const float est =
+      share ? -fabsf(0.5f * logf(fminf(fmaxf(share[(size_t)k * N + i], eps), 1.0f))) : __int_as_float(0xffffffff);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) hr[j] = j == i ? 0.0f : est;
+  __syncthreads();
   for (int q = threadIdx.x; q < K; q += blockDim.x) {
     const int j = ids[q];
-    if (j >= 0 && j < N && j != i) hr[j] = -0.5f * logf(fmaxf(pr[q], eps));
+    if (j >= 0 && j < N && j != i) hr[j] = fabsf(0.5f * logf(fminf(fmaxf(pr[q], eps), 1.0f)));
+  }
+}
+
+// d = |h| + |h^T| in place over D stacked N x N matrices of half distances, with trust bits:
+// bit j of word j/32 of mask row i (mask [D][N][wpr], wpr = ceil(N/32)) is 1 where both halves are
+// chain values (sign bit clear) and either both targets have dense rows (dense_row[i] and
+// dense_row[j]) or d_ij <= d_trust.  A NaN half (no pool) leaves d NaN and the bit 0.  Tiles as in
+// symmetrize_kernel; a warp holds 32 consecutive columns of one row, so one ballot gives a word.
+__global__ void symmetrize_trust_kernel(float* __restrict__ d, int N, const uint8_t* __restrict__ dense_row,
+                                        float d_trust, uint32_t* __restrict__ mask, int wpr) {
+  const int bx = blockIdx.x, by = blockIdx.y;
+  if (bx > by) return;
+  float* m = d + (size_t)blockIdx.z * N * N;
+  uint32_t* mk = mask ? mask + (size_t)blockIdx.z * N * wpr : nullptr;
+  __shared__ float A[32][33], B[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const int ra = bx * 32 + k, ca = by * 32 + tx;
+    const int rb = by * 32 + k, cb = bx * 32 + tx;
+    A[k][tx] = (ra < N && ca < N) ? m[(size_t)ra * N + ca] : 0.0f;
+    B[k][tx] = (rb < N && cb < N) ? m[(size_t)rb * N + cb] : 0.0f;
+  }
+  __syncthreads();
+  auto one = [&](int row, int col, float a, float b) {
+    const bool in = row < N && col < N;
+    const float v = row == col ? 0.0f : fabsf(a) + fabsf(b);
+    const bool chain = !signbit(a) && !signbit(b) && v == v;
+    const bool dense = dense_row && in && dense_row[row] && dense_row[col];
+    const bool t = in && row != col && chain && (dense || v <= d_trust);
+    if (in) m[(size_t)row * N + col] = v;
+    const uint32_t word = __ballot_sync(0xffffffffu, t);
+    if (mk && tx == 0 && row < N) mk[(size_t)row * wpr + (col >> 5)] = word;
+  };
+  for (int k = ty; k < 32; k += 8) {
+    one(bx * 32 + k, by * 32 + tx, A[k][tx], B[tx][k]);
+    if (bx != by) one(by * 32 + k, bx * 32 + tx, B[k][tx], A[tx][k]);
   }
 }
 
@@ -348,7 +412,7 @@ __global__ void dense_rows_hdist_kernel(const float* __restrict__ prod, int nf, 
   float* o = h + ((size_t)k * N + i) * N;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     const float q = Z > 0.0f ? a[j] * invZ : eps;
-    o[j] = j == i ? 0.0f : -0.5f * logf(fmaxf(q, eps));
+    o[j] = j == i ? 0.0f : fabsf(0.5f * logf(fminf(fmaxf(q, eps), 1.0f)));  // +0.0 at q = 1 (a chain value)
   }
 }
 

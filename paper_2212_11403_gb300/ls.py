@@ -100,7 +100,7 @@ def _load():
         "ls_mlp_train": ([P, P, P, ctypes.c_int64, I, I, ctypes.c_float, ctypes.c_uint64, P, P], I),
         "ls_propose_window": ([P, I, I, P, P, P], I),
         "ls_propose": ([P, I, I, P, P, P], I),
-        "ls_sparse_run_all": ([P, P, I, I, I, I, P, I, P, ctypes.c_float, P, P, P, P, P], I),
+        "ls_sparse_run_all": ([P, P, I, I, I, I, P, I, P, ctypes.c_float, P, P, P, P, ctypes.c_float, P, P, P], I),
         "ls_set_profiling": ([P, I], I),
         "ls_profile_read": ([P, P, P], I),
     }
@@ -413,8 +413,9 @@ def ls_propose(ctx, C, K, mlp, idx_out, stream=None):
 
 
 def ls_sparse_run_all(ctx, idx, K, WS, decode_loci, d_out, lost_tol=-1.0, lost_out=None, status_out=None,
-                      lookahead=2, pool=True, stream=None):
-    """Returns (rc, pac of the restricted chains, number of dense-fallback targets)."""
+                      lookahead=2, pool=True, d_trust=float("inf"), trust_out=None, pout_out=None, stream=None):
+    """Returns (rc, pac of the restricted chains, number of dense-fallback targets).  trust_out: an
+    int32 CUDA tensor [D, N, ceil(N/32)] receiving the trust bits (see include/ls.h)."""
     import torch
     dl = np.ascontiguousarray(decode_loci, dtype=np.int32)
     pac = ctypes.c_double()
@@ -423,8 +424,17 @@ def ls_sparse_run_all(ctx, idx, K, WS, decode_loci, d_out, lost_tol=-1.0, lost_o
                                        dl.ctypes.data_as(ctypes.c_void_p), dl.size, _dev(d_out, torch.float32, "d_out"),
                                        ctypes.c_float(lost_tol), _dev(lost_out, torch.float32, "lost_out"),
                                        ctypes.byref(pac), _dev(status_out, torch.int32, "status_out"), ctypes.byref(nf),
-                                       _stream(stream)))
+                                       ctypes.c_float(d_trust), _dev(trust_out, torch.int32, "trust_out"),
+                                       _dev(pout_out, torch.float32, "pout_out"), _stream(stream)))
     return rc, pac.value, nf.value
+
+
+def trust_bits(mask, N):
+    """Unpack trust_out words ([D, N, ceil(N/32)] int32 tensor) into a bool tensor [D, N, N]."""
+    import torch
+    m = mask.to(torch.int64) & 0xFFFFFFFF
+    bits = (m.unsqueeze(-1) >> torch.arange(32, device=mask.device)) & 1
+    return bits.reshape(mask.shape[0], mask.shape[1], -1)[:, :, :N].bool()
 
 
 def ls_set_profiling(ctx, enable=True):

@@ -21,6 +21,7 @@ import numpy as np
 from . import ls, proposal, synth
 
 P_FP32 = 2 * 128 * 152 * 2070e6  # FP32 FMA pipe, FLOP/s at the maximum SM clock
+D_TRUST = float("inf")  # distance bound of the sparse path's trusted entries
 
 
 def timed(fn, reps=1):
@@ -128,16 +129,17 @@ def measure_sparse():
                        train_seconds=t_train, train_loss=loss)
             idx = torch.empty((N, Wn, K), dtype=torch.int32, device="cuda")
             ds = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+            tm = torch.empty((len(loci), N, (N + 31) // 32), dtype=torch.int32, device="cuda")
             for name, m in (("raw", None), ("mlp", net)):
                 tp = timed(lambda: ls.ls_propose(ctx, C, K, m, idx))
-                ts = timed(lambda: ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds))
-                rec[name] = dict(propose_seconds=tp, sparse_seconds=ts, total_seconds=tp + ts,
-                                 coverage=float(torch.isfinite(ds).float().mean()))
+                ts = timed(lambda: ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds, d_trust=D_TRUST, trust_out=tm))
+                fin = ls.trust_bits(tm, N)
+                rec[name] = dict(propose_seconds=tp, sparse_seconds=ts, total_seconds=tp + ts, d_trust=D_TRUST,
+                                 trusted=float(fin.float().mean()))
                 if with_dense:
                     if "dense_seconds" not in rec:
                         dd = torch.empty_like(ds)
                         rec["dense_seconds"] = timed(lambda: ls.ls_run_all(ctx, loci, dd, want_pac=False))
-                    fin = torch.isfinite(ds)
                     e = (ds - dd).abs()[fin]
                     smp = e[torch.randperm(e.numel(), device=e.device)[:4000000]]
                     q = torch.quantile(smp, torch.tensor([0.5, 0.9, 0.99], device=e.device)).tolist()

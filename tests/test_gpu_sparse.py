@@ -157,10 +157,10 @@ def test_mlp_topk_keeps_the_best_scores(ls):
         assert np.all(np.diff(idx[i, wi]) > 0) and i not in idx[i, wi]
 
 
-def sparse_stats(ds, dd):
-    """coverage and |d_sparse - d_dense| statistics over the covered entries."""
+def sparse_stats(ds, dd, trust):
+    """coverage (trusted entries) and |d_sparse - d_dense| statistics over the trusted entries."""
     import torch
-    fin = torch.isfinite(ds)
+    fin = trust
     e = (ds - dd).abs()[fin]
     sample = e[torch.randperm(e.numel(), device=e.device)[:2000000]]
     q = torch.quantile(sample, torch.tensor([0.5, 0.9, 0.99], device=e.device)).tolist()
@@ -187,11 +187,13 @@ def test_sparse_distances_against_dense_and_fallback(ls):
         ls.ls_propose(ctx, K, K, None, idx)
         ds = torch.empty_like(dd)
         lost = torch.empty(N, dtype=torch.float32, device="cuda")
-        rc, pac, nf = ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds, lost_tol=-1.0, lost_out=lost)
-        st0 = sparse_stats(ds, dd)
+        tm = torch.empty((len(loci), N, (N + 31) // 32), dtype=torch.int32, device="cuda")
+        rc, pac, nf = ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds, lost_tol=-1.0, lost_out=lost, trust_out=tm)
+        assert bool(torch.isfinite(ds).all())   # complete: outside donors carry the pool's share
+        st0 = sparse_stats(ds, dd, ls.trust_bits(tm, N))
         lost_h = lost.cpu().numpy()
         df = torch.empty_like(dd)
-        rc2, _, nf2 = ls.ls_sparse_run_all(ctx, idx, K, 256, loci, df, lost_tol=tol)
+        rc2, _, nf2 = ls.ls_sparse_run_all(ctx, idx, K, 256, loci, df, lost_tol=tol, trust_out=tm)
         torch.cuda.synchronize()
         fb = np.flatnonzero(~(lost_h <= tol))
         assert nf2 == fb.size
@@ -199,7 +201,7 @@ def test_sparse_distances_against_dense_and_fallback(ls):
             sub = df[:, fb][:, :, fb]
             ref = dd[:, fb][:, :, fb]
             assert d_err(sub.cpu().numpy(), ref.cpu().numpy().astype(np.float64)) <= 1e-5
-        st1 = sparse_stats(df, dd)
+        st1 = sparse_stats(df, dd, ls.trust_bits(tm, N))
     finally:
         ls.ls_destroy(ctx)
     assert rc == 0 and nf == 0
@@ -238,9 +240,10 @@ def test_trained_proposal_against_raw_counts(ls):
             ls.ls_propose(ctx, C, K, net, idx)
             mass = proposal.set_mass(idx, P, wins)
             ds = torch.empty_like(dd)
-            ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds)
+            tm = torch.empty((len(loci), N, (N + 31) // 32), dtype=torch.int32, device="cuda")
+            ls.ls_sparse_run_all(ctx, idx, K, 256, loci, ds, trust_out=tm)
             res[name] = dict(mass_mean=float(mass.mean()), mass_q01=float(torch.quantile(mass.flatten(), 0.01)),
-                             **sparse_stats(ds, dd))
+                             **sparse_stats(ds, dd, ls.trust_bits(tm, N)))
     finally:
         ls.ls_destroy(ctx)
         ls.ls_mlp_destroy(m)
@@ -271,9 +274,12 @@ def test_restricted_chain_matches_its_oracle(ls, lookahead, pool):
     try:
         ls.ls_set_params(ctx, w["rho"], w["mu"])
         d = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
-        ls.ls_sparse_run_all(ctx, torch.from_numpy(S).cuda(), K, WS, loci, d, lookahead=lookahead, pool=pool)
+        tm = torch.empty((len(loci), N, (N + 31) // 32), dtype=torch.int32, device="cuda")
+        ls.ls_sparse_run_all(ctx, torch.from_numpy(S).cuda(), K, WS, loci, d, lookahead=lookahead, pool=pool,
+                             trust_out=tm)
         torch.cuda.synchronize()
         d = d.cpu().numpy().astype(np.float64)
+        trust = ls.trust_bits(tm, N).cpu().numpy()
     finally:
         ls.ls_destroy(ctx)
     sets = op.lookahead_sets(S, lookahead) if lookahead else S
@@ -282,13 +288,23 @@ def test_restricted_chain_matches_its_oracle(ls, lookahead, pool):
     for k, l in enumerate(loci):
         v = l // WS
         H = np.full((N, N), np.nan)
+        inset = np.zeros((N, N), dtype=bool)
         for i in range(N):
             for j in sets[i, v]:
                 if j >= 0:
+                    inset[i, j] = True
+            for j in range(N):
+                if j != i and (inset[i, j] or pool):
                     H[i, j] = -0.5 * np.log(max(p[i, k, j], eps))
         ref = H + H.T
         np.fill_diagonal(ref, 0.0)
+        # with the pool every entry is defined (outside donors carry the pool's share); without it
+        # entries with an outside donor on either side are NaN
         assert np.array_equal(np.isfinite(d[k]), np.isfinite(ref)), l
         fin = np.isfinite(ref)
         err = np.abs(d[k][fin] - ref[fin]) / np.maximum(1.0, np.abs(ref[fin]))
         assert float(err.max()) <= D_TOL, (l, float(err.max()))
+        # trust bits (no distance bound given): both halves are chain posteriors
+        both = inset & inset.T
+        np.fill_diagonal(both, False)
+        np.testing.assert_array_equal(trust[k], both)

@@ -145,11 +145,9 @@ def test_pooled_sparse_oracle_is_exact_when_outside_donors_are_identical():
         sets[j, :, :N - 1 if N - 1 <= 4 else 4] = [k for k in range(N) if k != j][:4]
     p = op.sparse_posteriors(h, rho, 0.05, sets, 10, [0, 17, 39], pool=True)
     ref = oracle.run(h, rho, 0.05, [0, 17, 39], targets=[i], want=("post",))["post"][0]
-    # the pool holds the outside mass exactly, so the set donors' posteriors differ from the dense
-    # ones only by the outside posterior mass, a common factor per locus
-    for k in range(3):
-        ps, pd = p[i, k, 1:5], ref[k, 1:5]
-        np.testing.assert_allclose(ps / ps.sum(), pd / pd.sum(), rtol=1e-12)
+    # the pool holds the outside mass exactly and shares its posterior equally among identical
+    # donors, so every donor's posterior is the dense one
+    np.testing.assert_allclose(p[i], ref, rtol=1e-12, atol=1e-300)
 
 
 def _changing_sets(N, Wn, base, extra_choices, i, rng):
@@ -173,7 +171,8 @@ def test_pooled_chain_is_an_exact_lumping_with_changing_sets():
     mass exactly, a donor that leaves hands its mass to the pool, and an entering donor's
     pool share is its dense value.  The pooled chain is then an exact lumping of the dense chain
     even as donors of the identical group enter and leave the set between windows, and the set
-    donors' posteriors equal the dense ones divided by the dense posterior mass of the set."""
+    donors' posteriors equal the dense ones, and so do the outside donors' equal shares of the
+    pool's posterior mass."""
     import oracle
     rng = np.random.default_rng(41)
     L, N, ws = 36, 10, 4
@@ -191,10 +190,7 @@ def test_pooled_chain_is_an_exact_lumping_with_changing_sets():
         assert changes >= 3
         p = op.sparse_posteriors(h, rho, mu, sets, ws, loci, pool=True)[i]
         ref = oracle.run(h, rho, mu, loci, targets=[i], want=("post",))["post"][0]
-        for k, l in enumerate(loci):
-            S = [int(j) for j in sets[i, l // ws] if j >= 0]
-            want = ref[k, S] / ref[k, S].sum()
-            np.testing.assert_allclose(p[k, S], want, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(p, ref, rtol=1e-12, atol=1e-300)
 
 
 def test_pooled_chain_matches_brute_force_of_its_definition():
@@ -223,6 +219,9 @@ def test_pooled_chain_matches_brute_force_of_its_definition():
         marg = enumerate_pooled(h, rho, mu, [[int(j) for j in sets[i, l // ws] if j >= 0] for l in range(L)], i)
         for l in range(L):
             S = [int(j) for j in sets[i, l // ws] if j >= 0]
-            z = sum(marg[l].get(j, 0.0) for j in S)
+            out = [j for j in range(N) if j != i and j not in S]
             for j in S:
-                assert abs(p[l, j] - marg[l].get(j, 0.0) / z) <= 1e-12, (trial, l, j)
+                assert abs(p[l, j] - marg[l].get(j, 0.0)) <= 1e-12, (trial, l, j)
+            for j in out:   # an equal share of the pool state's posterior
+                assert abs(p[l, j] - marg[l].get("o", 0.0) / len(out)) <= 1e-12, (trial, l, j)
+            assert abs(p[l].sum() - 1.0) <= 1e-12
