@@ -929,7 +929,9 @@ int ls_run_all(ls_ctx* ctx, const int32_t* decode_loci, int32_t D, float* d_out,
   if (prof) CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
   ctx->launches[2] = ctx->launches[3] = 0;
   if (D > 0) {
-    lsk::decode_kernel<<<dim3(N, D), 256, 0, s>>>(dd, N);
+    lsk::DecodeLoci dl;
+    for (int k = 0; k < D; ++k) dl.l[k] = decode_loci[k];
+    lsk::decode_kernel<<<dim3(N, D), 256, 0, s>>>(dd, N, ctx->bits, ctx->row_words, ctx->thm, ctx->thx, dl);
     CUDA_TRY(cudaGetLastError());
     ctx->launches[2] = 1;
   }
@@ -1293,7 +1295,7 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
   int* wos;
   uint8_t* dense_row;
   if ((rc = db.get(&P, (size_t)D * N * K)) || (rc = db.get(&lost, N)) || (rc = db.get(&logs, N)) ||
-      (rc = db.get(&stat, N)) || (rc = db.get(&wos, D)) || (rc = db.get(&dense_row, N)) ||
+      (rc = db.get(&stat, N)) || (rc = db.get(&wos, 2 * D)) || (rc = db.get(&dense_row, N)) ||
       (pool && ((rc = db.get(&poolf, (size_t)D * N)) || (rc = db.get(&share, (size_t)D * N)))))
     return rc;
   CUDA_TRY(cudaMemsetAsync(dense_row, 0, N, s));
@@ -1307,9 +1309,14 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
     K = (lookahead + 1) * K;
     if ((rc = db.get(&P, (size_t)D * N * K))) return rc;  // the posteriors need the wider rows
   }
-  std::vector<int> wh(D);
-  for (int k = 0; k < D; ++k) wh[k] = decode_loci[k] / WS;
-  CUDA_TRY(cudaMemcpyAsync(wos, wh.data(), sizeof(int) * D, cudaMemcpyHostToDevice, s));
+  std::vector<int> wh(2 * D);  // window of each decode slot, then the decode loci themselves
+  for (int k = 0; k < D; ++k) {
+    wh[k] = decode_loci[k] / WS;
+    wh[D + k] = decode_loci[k];
+  }
+  CUDA_TRY(cudaMemcpyAsync(wos, wh.data(), sizeof(int) * 2 * D, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));  // wh is a host temporary
+  const int* wos_loci = wos + D;
   CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(uint32_t) * N, s));
   // haplotype-major words: each set entry's 32 bits of a block of loci are one load
   uint32_t* hw;
@@ -1409,7 +1416,7 @@ int ls_sparse_run_all(ls_ctx* ctx, const int32_t* idx, int32_t K, int32_t WS, in
     }
     p.alpha_dec = prod;
     if ((rc = run_list(ctx, p, tl, nf, s))) return rc;
-    e = ls_launch_dense_rows_hdist(prod, nf, N, tl, D, d_out, s);
+    e = ls_launch_dense_rows_hdist(prod, nf, N, tl, ctx->bits, ctx->row_words, ctx->thm, ctx->thx, wos_loci, D, d_out, s);
     if (e != cudaSuccess) return fail(LS_ERR_CUDA, "fallback distance launch: %s", cudaGetErrorString(e));
     std::vector<uint8_t> flag(N, 0);
     for (int t : fb) flag[t] = 1;
@@ -1593,7 +1600,9 @@ extern "C" int ls_run_all_noalloc(ls_ctx* ctx, const int32_t* decode_loci, int32
     }
   }
   if (D > 0) {
-    lsk::decode_kernel<<<dim3(N, D), 256, 0, s>>>(d_out, N);
+    lsk::DecodeLoci dl;
+    for (int k = 0; k < D; ++k) dl.l[k] = decode_loci[k];
+    lsk::decode_kernel<<<dim3(N, D), 256, 0, s>>>(d_out, N, ctx->bits, ctx->row_words, ctx->thm, ctx->thx, dl);
     CUDA_TRY(cudaGetLastError());
     const int nt = (N + 31) / 32;
     lsk::symmetrize_kernel<<<dim3(nt, nt, D), dim3(32, 8), 0, s>>>(d_out, N);

@@ -77,16 +77,32 @@ __global__ void posterior_kernel(const float* __restrict__ alpha, const float* _
   }
 }
 
-// Normalise the products alpha * beta that the backward pass left at D decode loci ([D][N][N],
-// row i = recipient i) into half distances -log(max(p, eps))/2 with p of Eq. postprob, in place.
-// A zero normaliser gives p = eps for every donor (Sec. 2.2).  Grid (N, D), one CTA per row.
-__global__ void decode_kernel(float* __restrict__ prod, int N) {
+// Decode loci of the D slots of a fused pipeline (at most kMaxStore), passed by value.
+struct DecodeLoci {
+  int l[kMaxStore];
+};
+
+// Normalise the products that the backward pass left at D decode loci ([D][N][N], row i = recipient
+// i) into half distances -log(max(p, eps))/2 with p of Eq. postprob, in place.  A product is
+// alpha^l t^l (times a power of two), t = theta beta the backward tile after its update at l, so
+// each entry is first divided by its emission theta^l_ij (1 - mu where donor j carries the target's
+// allele at l, mu elsewhere, read from the packed row; a zero theta means alpha = 0 too, and the
+// entry is 0).  A zero normaliser gives p = eps for every donor (Sec. 2.2).  Grid (N, D), one CTA
+// per row.
+__global__ void decode_kernel(float* __restrict__ prod, int N, const uint32_t* __restrict__ bits, int row_words,
+                              const float* __restrict__ thm, const float* __restrict__ thx, const DecodeLoci dl) {
   constexpr float eps = 2.220446049250313e-16f;
   const int r = blockIdx.x;
+  const int l = dl.l[blockIdx.y];
+  const uint32_t* row = bits + (size_t)l * row_words;
+  const uint32_t ai = (row[r >> 5] >> (r & 31)) & 1u;
+  const float tm = thm[l], tx = thx[l];
+  const float im = tm > 0.0f ? 1.0f / tm : 0.0f, ix = tx > 0.0f ? 1.0f / tx : 0.0f;
   float* a = prod + ((size_t)blockIdx.y * N + r) * N;
+  auto q = [&](int j) { return a[j] * ((((row[j >> 5] >> (j & 31)) & 1u) == ai) ? im : ix); };
   float s = 0.0f;
   for (int j = threadIdx.x; j < N; j += blockDim.x)
-    if (j != r) s += a[j];
+    if (j != r) s += q(j);
   __shared__ float red[32];
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -100,7 +116,7 @@ __global__ void decode_kernel(float* __restrict__ prod, int N) {
   const float Z = red[0];
   const float invZ = Z > 0.0f ? 1.0f / Z : 0.0f;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const float p = Z > 0.0f ? a[j] * invZ : eps;
+    const float p = Z > 0.0f ? q(j) * invZ : eps;
     a[j] = j == r ? 0.0f : -0.5f * logf(fmaxf(p, eps));
   }
 }

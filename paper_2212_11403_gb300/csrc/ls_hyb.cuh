@@ -231,11 +231,14 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
       store_state(p.store + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f);
       pend_slot = -1;
     }
-    if (DIR == 1 && (is_store || save_here)) {
-      // beta^l = c t^{l+1} + rho; when decoding, alpha^l beta^l overwrites alpha^l in place
+    if (DIR == 1 && pend_slot >= 0) {  // decode product of the previous locus: alpha^l t^l, t = theta beta
+      store_state(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
+      pend_slot = -1;
+    }
+    if (DIR == 1 && ((is_store && p.store) || save_here)) {
+      // beta^l = c t^{l+1} + rho (tables and stored rows)
       const size_t so = (size_t)(is_store ? p.store_slot[store_next] : 0) * p.state_rows * N;
-      store_state((is_store && p.store) ? p.store + so : nullptr, (is_store && p.alpha_dec) ? p.alpha_dec + so : nullptr,
-                  save_here ? p.state : nullptr, true, c, r);
+      store_state((is_store && p.store) ? p.store + so : nullptr, nullptr, save_here ? p.state : nullptr, true, c, r);
     }
 
     // match bits of the thread's positions (bit o of aw[o >> 5] <-> position d0 + o)
@@ -272,6 +275,8 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     if (DIR == 0) {  // alpha^l is stored at the top of the next step (or after the loop)
       pend_slot = is_store && p.store ? p.store_slot[store_next] : -1;
       pend_save = save_here;
+    } else {  // decoding: alpha^l times t^l at the top of the next step (decode_kernel divides by theta)
+      pend_slot = is_store && p.alpha_dec ? p.store_slot[store_next] : -1;
     }
     if (is_store) {
       ++store_next;
@@ -298,6 +303,8 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     }
     sig_prev = sig;
   }
+  if (DIR == 1 && pend_slot >= 0)  // decode product of the last locus
+    store_state(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
   if (DIR == 0 && (pend_slot >= 0 || pend_save))
     store_state(pend_slot >= 0 ? p.store + (size_t)pend_slot * p.state_rows * N : nullptr, nullptr,
                 pend_save ? p.state : nullptr, false, 0.f, 0.f);

@@ -39,7 +39,8 @@ cudaError_t ls_launch_sparse_hdist(const float* P, const int32_t* idx, int N, in
                                    const float* share, int D, float* h, cudaStream_t s);
 cudaError_t ls_launch_symmetrize_trust(float* d, int N, int D, const uint8_t* dense_row, float d_trust, uint32_t* mask,
                                        cudaStream_t s);
-cudaError_t ls_launch_dense_rows_hdist(const float* prod, int nf, int N, const int* tlist, int D, float* h,
+cudaError_t ls_launch_dense_rows_hdist(const float* prod, int nf, int N, const int* tlist, const uint32_t* bits,
+                                       int row_words, const float* thm, const float* thx, const int* dloci, int D, float* h,
                                        cudaStream_t s);
 
 struct ls_ctx {

@@ -92,7 +92,8 @@ struct PropParams {
   int store_slot[kMaxStore];  // output slot of each store locus
   float* store;           // [slots][state_rows][N] alpha (fwd) / beta (bwd) at store loci
   float* alpha_dec;       // backward decode: alpha at the same loci, same layout (may be null);
-                          // overwritten in place by alpha * beta (normalised by decode_kernel)
+                          // multiplied in place by t = theta beta (times 2^100): decode_kernel
+                          // divides by theta and normalises
   // forward statistic passes (ST > 0): w_j = alpha_j E[S | Z = j, h_0..l] for an additive S
   const float* gam;       // [L-1] weight of a recombination at interval m (ST 1)
   const uint8_t* reset;   // [L-1] 1: interval m opens a new group, w restarts from 0 (ST 1)
@@ -602,13 +603,14 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       pend_slot = -1;
     }
 
-    if (DIR == 1 && (is_store || save_here)) {
-      // beta^l = c t^{l+1} + rho, the pre-emission value; when decoding, alpha^l beta^l
-      // overwrites alpha^l in place (normalised by the decode kernel)
-      const int slot = is_store ? p.store_slot[store_next] : 0;
-      const size_t so = (size_t)slot * p.state_rows * N;
-      store_tile((is_store && p.store) ? p.store + so : nullptr, (is_store && p.alpha_dec) ? p.alpha_dec + so : nullptr,
-                 save_here ? p.state : nullptr, true, c, r);
+    if (DIR == 1 && pend_slot >= 0) {  // decode product of the previous locus: alpha^l t^l, t = theta beta
+      store_tile(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
+      pend_slot = -1;
+    }
+    if (DIR == 1 && ((is_store && p.store) || save_here)) {
+      // beta^l = c t^{l+1} + rho, the pre-emission value (tables and stored rows)
+      const size_t so = (size_t)(is_store ? p.store_slot[store_next] : 0) * p.state_rows * N;
+      store_tile((is_store && p.store) ? p.store + so : nullptr, nullptr, save_here ? p.state : nullptr, true, c, r);
     }
 
     // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
@@ -746,6 +748,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     if (DIR == 0) {  // alpha^l is stored at the top of the next step (or after the loop)
       pend_slot = is_store && p.store ? p.store_slot[store_next] : -1;
       pend_save = save_here;
+    } else {  // decoding: alpha^l is multiplied by t^l = theta^l beta^l at the top of the next step; the
+              // decode kernel divides the product by theta^l (it reads the locus' alleles)
+      pend_slot = is_store && p.alpha_dec ? p.store_slot[store_next] : -1;
     }
     if (is_store) {
       ++store_next;
@@ -780,6 +785,8 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     sig_prev = sig;
   }
 
+  if (DIR == 1 && pend_slot >= 0)  // decode product of the last locus
+    store_tile(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
   if (DIR == 0 && (pend_slot >= 0 || pend_save)) {  // alpha of the last locus and the state, one pass
     store_tile(pend_slot >= 0 ? p.store + (size_t)pend_slot * p.state_rows * N : nullptr, nullptr,
                pend_save ? p.state : nullptr, false, 0.f, 0.f);

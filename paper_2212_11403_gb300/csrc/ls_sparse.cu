@@ -47,9 +47,10 @@ cudaError_t ls_launch_symmetrize_trust(float* d, int N, int D, const uint8_t* de
   return cudaGetLastError();
 }
 
-cudaError_t ls_launch_dense_rows_hdist(const float* prod, int nf, int N, const int* tlist, int D, float* h,
+cudaError_t ls_launch_dense_rows_hdist(const float* prod, int nf, int N, const int* tlist, const uint32_t* bits,
+                                       int row_words, const float* thm, const float* thx, const int* dloci, int D, float* h,
                                        cudaStream_t s) {
-  lsk::dense_rows_hdist_kernel<<<dim3(nf, D), 256, 0, s>>>(prod, nf, N, tlist, h);
+  lsk::dense_rows_hdist_kernel<<<dim3(nf, D), 256, 0, s>>>(prod, nf, N, tlist, bits, row_words, thm, thx, dloci, h);
   return cudaGetLastError();
 }
 

@@ -386,17 +386,26 @@ __global__ void symmetrize_trust_kernel(float* __restrict__ d, int N, const uint
   }
 }
 
-// Dense fallback rows: products alpha * beta of nf listed targets ([D][nf][N]) normalised into
-// half distances of rows tlist[r] of h ([D][N][N]).  grid (nf, D), 256 threads.
+// Dense fallback rows: products alpha^l t^l (t = theta beta, the dense backward's decode product)
+// of nf listed targets ([D][nf][N]) divided by theta^l (the locus' alleles from the packed rows,
+// decode locus of slot k in dloci[k]) and normalised into half distances of rows tlist[r] of h
+// ([D][N][N]).  grid (nf, D), 256 threads.
 __global__ void dense_rows_hdist_kernel(const float* __restrict__ prod, int nf, int N, const int* __restrict__ tlist,
+                                        const uint32_t* __restrict__ bits, int row_words, const float* __restrict__ thm,
+                                        const float* __restrict__ thx, const int* __restrict__ dloci,
                                         float* __restrict__ h) {
   constexpr float eps = 2.220446049250313e-16f;
   const int r = blockIdx.x, k = blockIdx.y;
   const int i = tlist[r];
-  const float* a = prod + ((size_t)k * nf + r) * N;
+  const int l = dloci[k];
+  const uint32_t* row = bits + (size_t)l * row_words;
+  const uint32_t ai = (row[i >> 5] >> (i & 31)) & 1u;
+  const float im = thm[l] > 0.0f ? 1.0f / thm[l] : 0.0f, ix = thx[l] > 0.0f ? 1.0f / thx[l] : 0.0f;
+  const float* a0 = prod + ((size_t)k * nf + r) * N;
+  auto a = [&](int j) { return a0[j] * ((((row[j >> 5] >> (j & 31)) & 1u) == ai) ? im : ix); };
   float s = 0.0f;
   for (int j = threadIdx.x; j < N; j += blockDim.x)
-    if (j != i) s += a[j];
+    if (j != i) s += a(j);
   __shared__ float red[32];
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -411,7 +420,7 @@ __global__ void dense_rows_hdist_kernel(const float* __restrict__ prod, int nf, 
   const float invZ = Z > 0.0f ? 1.0f / Z : 0.0f;
   float* o = h + ((size_t)k * N + i) * N;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const float q = Z > 0.0f ? a[j] * invZ : eps;
+    const float q = Z > 0.0f ? a(j) * invZ : eps;
     o[j] = j == i ? 0.0f : fabsf(0.5f * logf(fminf(fmaxf(q, eps), 1.0f)));  // +0.0 at q = 1 (a chain value)
   }
 }
