@@ -6,12 +6,14 @@
 // ([QS][512] float4, so a warp's 16-byte accesses are contiguous).  With QR = 12 the registers hold
 // 24576 positions per target and shared memory up to 16 x 8 KB more (N <= 57344).  Per locus a
 // thread reads the packed bits of its positions from the (L2-resident) packed row one locus ahead,
-// XORs them with the target's allele and selects theta per cell by a bit test (no emission table,
+// XORs them with the target's allele and takes the emission per cell by a bit test (no emission table,
 // so shared-memory traffic is the state of the QS quads only: 8 bytes per cell there, none in the
-// register part), and updates x <- theta (c x + r) with FFMA + FMUL + FADD as f32x2 pairs.
-// Positions beyond N and the target's own position are forced to "mismatch": they all start at 0
-// and see the same c, r and theta = mu, so they hold one common value xs, replicated in every
-// thread, and the row sum subtracts n_junk * xs (the register-tile kernel's treatment).  The row
+// register part), and updates x <- theta (c x + r) as (c b) x + r b with b = max(1-mu, mu), followed
+// by a predicated multiply by min(1-mu, mu) / b on the cells whose emission is the smaller value
+// (FFMA2, FMUL, FADD2).  Positions beyond N and the target's own position always take the smaller
+// factor: they all start at 0 and see the same operations, so they hold one common value xs,
+// replicated in every thread, and the row sum subtracts n_junk * xs (the register-tile kernel's
+// treatment).  The row
 // sum is a shuffle tree, one CTA barrier and a 16-entry sum; FP64 log scales are accumulated by
 // thread 0.
 //
@@ -184,6 +186,7 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   }
   double lgs = (tid == 0 && p.logs && !p.init) ? p.logs[row] : 0.0;
   float lsum = 0.0f, lerr = 0.0f;  // logs of the normalisers since the last fold into lgs
+  float u_base = 1.0f, u_ratio = 0.0f;  // emission base and ratio (per locus only with a per-locus mu)
   uint32_t sts = 0u;
   int store_next = 0;
   int next_store_l = p.n_store > 0 ? p.store_loci[0] : -1;
@@ -241,36 +244,50 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
       store_state((is_store && p.store) ? p.store + so : nullptr, nullptr, save_here ? p.state : nullptr, true, c, r);
     }
 
+    // Emission as base x f, base = max(1-mu, mu), f in {1, ratio}: a cell is (c base) x + r base,
+    // then multiplied by ratio where f = ratio (a predicated multiply, no select).  The "small" bits
+    // (f = ratio) are the mismatches, or the matches when mu > 1/2; junk positions have bit 0.
+    if (p.mu_vec || step == 0) {
+      u_base = fmaxf(thm, thx);
+      u_ratio = u_base > 0.0f ? __fdiv_rn(fminf(thm, thx), u_base) : 0.0f;
+    }
     // match bits of the thread's positions (bit o of aw[o >> 5] <-> position d0 + o)
-    const uint32_t inv = ctb ? 0u : 0xffffffffu;
+    const uint32_t inv = (ctb ? 0u : 0xffffffffu) ^ (thm < thx ? 0xffffffffu : 0u);
     uint32_t aw[NWA];
 #pragma unroll
     for (int k = 0; k < NWA; ++k) aw[k] = (funnel(cw[k], cw[k + 1], sh) ^ inv) & vm[k];
-    const f2 C2 = make_float2(c, c), R2 = make_float2(r, r);
+    const float cu = c * u_base, ru = r * u_base;
+    const f2 C2 = make_float2(cu, cu), R2 = make_float2(ru, ru);
     f2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    auto emit = [&](f2 u01, f2 u23, uint32_t w, int b, f2& o01, f2& o23) {
+      float a0 = u01.x, a1 = u01.y, a2 = u23.x, a3 = u23.y;
+      if (!((w >> b) & 1u)) a0 = __fmul_rn(a0, u_ratio);
+      if (!((w >> (b + 1)) & 1u)) a1 = __fmul_rn(a1, u_ratio);
+      if (!((w >> (b + 2)) & 1u)) a2 = __fmul_rn(a2, u_ratio);
+      if (!((w >> (b + 3)) & 1u)) a3 = __fmul_rn(a3, u_ratio);
+      o01 = make_float2(a0, a1);
+      o23 = make_float2(a2, a3);
+    };
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const uint32_t w = aw[(4 * q) >> 5];
       const int b = (4 * q) & 31;
-      const f2 t01 = make_float2((w >> b) & 1u ? thm : thx, (w >> (b + 1)) & 1u ? thm : thx);
-      const f2 t23 = make_float2((w >> (b + 2)) & 1u ? thm : thx, (w >> (b + 3)) & 1u ? thm : thx);
       if (q < QR) {
         const int qr = q < QR ? q : 0;
-        x[qr][0] = __fmul2_rn(t01, __ffma2_rn(C2, x[qr][0], R2));
-        x[qr][1] = __fmul2_rn(t23, __ffma2_rn(C2, x[qr][1], R2));
+        emit(__ffma2_rn(C2, x[qr][0], R2), __ffma2_rn(C2, x[qr][1], R2), w, b, x[qr][0], x[qr][1]);
         acc0 = __fadd2_rn(acc0, x[qr][0]);
         acc1 = __fadd2_rn(acc1, x[qr][1]);
       } else {
         float4* sp = Xs + (q - QR) * T + tid;
         const float4 v = *sp;
-        const f2 y01 = __fmul2_rn(t01, __ffma2_rn(C2, make_float2(v.x, v.y), R2));
-        const f2 y23 = __fmul2_rn(t23, __ffma2_rn(C2, make_float2(v.z, v.w), R2));
+        f2 y01, y23;
+        emit(__ffma2_rn(C2, make_float2(v.x, v.y), R2), __ffma2_rn(C2, make_float2(v.z, v.w), R2), w, b, y01, y23);
         *sp = make_float4(y01.x, y01.y, y23.x, y23.y);
         acc0 = __fadd2_rn(acc0, y01);
         acc1 = __fadd2_rn(acc1, y23);
       }
     }
-    xs = thx * fmaf(c, xs, r);  // junk positions: theta = mu everywhere
+    xs = __fmul_rn(u_ratio, __fmaf_rn(cu, xs, ru));  // junk positions: always the "small" factor
 
     if (DIR == 0) {  // alpha^l is stored at the top of the next step (or after the loop)
       pend_slot = is_store && p.store ? p.store_slot[store_next] : -1;
