@@ -9,6 +9,7 @@
 #include "ls_internal.h"
 #include "ls_mlp.cuh"
 #include "ls_propose.cuh"
+#include "ls_mlp_tc.cuh"
 
 struct ls_mlp {
   int device = 0;
@@ -20,6 +21,7 @@ struct ls_mlp {
   __nv_bfloat16* w1t = nullptr;  // [256][16]
   __nv_bfloat16* w2t = nullptr;  // [256][256]
   float b3 = 0.0f;
+  int* err = nullptr;            // device word: a scorer wait ran out of time
 };
 
 namespace {
@@ -78,15 +80,34 @@ int refresh(ls_mlp* m) {
   return LS_OK;
 }
 
-lsk::MlpDev dev_view(const ls_mlp* m) {
-  lsk::MlpDev d;
+// Scores of n BF16 feature rows on the tensor cores (persistent CTAs, one per SM).
+int launch_scores(const ls_mlp* m, const __nv_bfloat16* X, long long n, float* scores, int nsm, cudaStream_t s) {
+  TRY(cudaFuncSetAttribute(lsk::mlp_score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lsk::kTcSmem));
+  lsk::MlpTcDev d;
   d.w1t = m->w1t;
   d.b1 = m->p + lsk::kOffB1;
   d.w2t = m->w2t;
   d.b2 = m->p + lsk::kOffB2;
   d.w3 = m->p + lsk::kOffW3;
   d.b3 = m->b3;
-  return d;
+  d.err = m->err;
+  const long long tiles = (n + lsk::kTcRows - 1) / lsk::kTcRows;
+  const int grid = (int)std::min<long long>(nsm, tiles);
+  lsk::mlp_score_tc_kernel<<<grid, lsk::kTcThreads, lsk::kTcSmem, s>>>(d, X, n, scores);
+  TRY(cudaGetLastError());
+  return LS_OK;
+}
+
+// the error word of the scorer: LS_ERR_DEVICE (and cleared) when a wait ran out of time
+int scorer_status(const ls_mlp* m, cudaStream_t s) {
+  int h = 0;
+  TRY(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  if (h) {
+    cudaMemsetAsync(m->err, 0, sizeof(int), s);
+    return fail(LS_ERR_DEVICE, "a wait of the tensor-core scorer ran out of time");
+  }
+  return LS_OK;
 }
 
 uint64_t splitmix(uint64_t& s) {
@@ -161,15 +182,18 @@ int ls_mlp_create(const float* params, uint64_t seed, ls_mlp** out) {
   int rc;
   if ((rc = dev_alloc(nullptr, (void**)&m->p, sizeof(float) * P)) || (rc = dev_alloc(nullptr, (void**)&m->g, sizeof(float) * P)) ||
       (rc = dev_alloc(nullptr, (void**)&m->m, sizeof(float) * P)) || (rc = dev_alloc(nullptr, (void**)&m->v, sizeof(float) * P)) ||
-      (rc = dev_alloc(nullptr, (void**)&m->w1t, 2 * 256 * lsk::kFeat)) || (rc = dev_alloc(nullptr, (void**)&m->w2t, 2 * 256 * 256))) {
+      (rc = dev_alloc(nullptr, (void**)&m->w1t, 2 * 256 * lsk::kFeat)) || (rc = dev_alloc(nullptr, (void**)&m->w2t, 2 * 256 * 256)) ||
+      (rc = dev_alloc(nullptr, (void**)&m->err, sizeof(int)))) {
     cudaFree(m->p);
     cudaFree(m->g);
     cudaFree(m->m);
     cudaFree(m->v);
     cudaFree(m->w1t);
+    cudaFree(m->w2t);
     delete m;
     return rc;
   }
+  cudaMemset(m->err, 0, sizeof(int));
   std::vector<float> h(P, 0.0f);
   if (params) {
     memcpy(h.data(), params, sizeof(float) * P);
@@ -203,6 +227,7 @@ int ls_mlp_destroy(ls_mlp* m) {
   cudaFree(m->v);
   cudaFree(m->w1t);
   cudaFree(m->w2t);
+  cudaFree(m->err);
   delete m;
   return LS_OK;
 }
@@ -228,14 +253,10 @@ int ls_mlp_forward(const ls_mlp* m, const float* X, int64_t n, float* scores, ls
   int rc;
   if ((rc = b.get(&Xb, (size_t)n * lsk::kFeat))) return rc;
   to_bf16_feat_kernel<<<blocks(n * lsk::kFeat), 256, 0, s>>>(X, n, Xb);
-  const int smem = lsk::mlp_smem_bytes();
-  TRY(cudaFuncSetAttribute(lsk::mlp_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
-  lsk::mlp_score_kernel<<<nsm, 256, smem, s>>>(dev_view(m), Xb, n, scores);
-  TRY(cudaGetLastError());
-  TRY(cudaStreamSynchronize(s));
-  return LS_OK;
+  if ((rc = launch_scores(m, Xb, n, scores, nsm, s))) return rc;
+  return scorer_status(m, s);
 }
 
 int ls_mlp_grad(ls_mlp* m, const float* X, const float* y, int32_t n, float* grad, double* loss, ls_stream_t stream) {
@@ -375,23 +396,18 @@ int ls_propose(ls_ctx* ctx, int32_t C, int32_t K, const ls_mlp* mlp, int32_t* id
   float* scores = nullptr;
   if ((rc = b.get(&cand, (size_t)N * Ce))) return rc;
   if (mlp && ((rc = b.get(&feat, (size_t)N * Ce * lsk::kFeat)) || (rc = b.get(&scores, (size_t)N * Ce)))) return rc;
-  const int smem = lsk::mlp_smem_bytes();
   int P = 1;
   while (P < Ce) P <<= 1;
   // topk needs P * 8 <= 16 KB of dynamic shared memory, within the default limit
-  if (mlp) TRY(cudaFuncSetAttribute(lsk::mlp_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   for (int w = 0; w < Wn; ++w) {
     if ((rc = stage1(pw, w, Ce, cand, Ce, feat, nullptr, s))) return rc;
-    if (mlp) {
-      lsk::mlp_score_kernel<<<ctx->num_sms, 256, smem, s>>>(dev_view(mlp), feat, (long long)N * Ce, scores);
-      TRY(cudaGetLastError());
-    }
+    if (mlp && (rc = launch_scores(mlp, feat, (long long)N * Ce, scores, ctx->num_sms, s))) return rc;
     // the K best (by score, or by the stage-1 order when there is no network) in ascending id order
     lsk::topk_kernel<<<N, 256, P * 8, s>>>(cand, mlp ? scores : nullptr, Ce, K, P, Wn, w, idx_out);
     TRY(cudaGetLastError());
   }
   TRY(cudaStreamSynchronize(s));
-  return LS_OK;
+  return mlp ? scorer_status(mlp, s) : LS_OK;
 }
 
 }  // extern "C"

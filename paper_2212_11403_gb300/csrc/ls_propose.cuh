@@ -1,5 +1,5 @@
 // ls_propose.cuh -- donor proposal for the sparse recursions: window match-count features, a
-// first-stage pre-filter, the MLP scorer (BF16 tensor-core MMA, FP32 accumulation) and top-K.
+// first-stage pre-filter and top-K (the MLP scorer on the tensor cores is in ls_mlp_tc.cuh).
 //
 // Windows hold 256 consecutive loci.  For haplotypes i, j and window w the feature is the match
 // count m_ij^w = n_w - popcount(h_i^w XOR h_j^w) (n_w = loci in the window).  Stage 1 keeps, for
@@ -19,8 +19,6 @@ constexpr int kPropWS = 256;       // loci per window
 constexpr int kFeat = 16;          // feature slots per candidate (7 used, zero padded to one MMA k-step)
 constexpr int kFeatUsed = 7;
 constexpr int kHidden = 256;
-constexpr int kMlpRows = 128;      // candidates per MLP tile
-constexpr int kHS = kHidden + 8;   // padded row stride (bf16) of the hidden tiles in shared memory
 
 // Haplotype-major window bits: hw[(w*N + i)*8 + k] bit b = allele of haplotype i at locus
 // w*256 + 32k + b (0 beyond L).  grid (ceil(N/32), 8, Wn), one warp: a 32 x 32 bit transpose by
@@ -204,123 +202,9 @@ __global__ void __launch_bounds__(256) stage1_kernel(Stage1Args a, int N, int Np
   for (int q = base_sel + tid; q < C; q += NT) cand[(size_t)i * C + q] = -1;
 }
 
-// MLP parameters on the device: BF16 transposed weights for the MMA, FP32 biases.
-struct MlpDev {
-  const __nv_bfloat16* w1t;  // [256][16]  w1t[n][k] = W1[k][n]
-  const float* b1;           // [256]
-  const __nv_bfloat16* w2t;  // [256][256] w2t[n][k] = W2[k][n]
-  const float* b2;           // [256]
-  const float* w3;           // [256]
-  float b3;
-};
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// scores[r] = w3 . relu(W2^T relu(W1^T x_r + b1) + b2) + b3 for n rows of BF16 features.
-// Persistent: each CTA stages the weights once and loops over tiles of 128 rows; warp w owns rows
-// 16w..16w+15 of a tile and all 256 hidden units (two halves of 128).
-__global__ void __launch_bounds__(256, 1) mlp_score_kernel(MlpDev m, const __nv_bfloat16* __restrict__ X, long long n,
-                                                            float* __restrict__ scores) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem);             // [256][kHS]
-  __nv_bfloat16* H1 = W2s + kHidden * kHS;                                 // [128][kHS]
-  __nv_bfloat16* W1s = H1 + kMlpRows * kHS;                                // [256][24]
-  __nv_bfloat16* Xs = W1s + kHidden * 24;                                  // [128][24]
-  float* bias = reinterpret_cast<float*>(Xs + kMlpRows * 24);              // b1[256], b2[256], w3[256]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, tg = lane & 3;
-  for (int e = tid; e < kHidden * kHidden; e += 256) W2s[(e >> 8) * kHS + (e & 255)] = m.w2t[e];
-  for (int e = tid; e < kHidden * kFeat; e += 256) W1s[(e >> 4) * 24 + (e & 15)] = m.w1t[e];
-  for (int e = tid; e < kHidden; e += 256) {
-    bias[e] = m.b1[e];
-    bias[256 + e] = m.b2[e];
-    bias[512 + e] = m.w3[e];
-  }
-  __syncthreads();
-  const long long ntile = (n + kMlpRows - 1) / kMlpRows;
-  for (long long t = blockIdx.x; t < ntile; t += gridDim.x) {
-    const long long r0 = t * kMlpRows;
-    for (int e = tid; e < kMlpRows * kFeat; e += 256) {
-      const int r = e >> 4, k = e & 15;
-      Xs[r * 24 + k] = r0 + r < n ? X[(r0 + r) * kFeat + k] : __float2bfloat16_rn(0.0f);
-    }
-    __syncthreads();
-    const int rw = 16 * warp;  // first row of this warp
-    // layer 1: one k-step of 16
-    uint32_t ax[4];
-    ax[0] = *reinterpret_cast<const uint32_t*>(Xs + (rw + g) * 24 + 2 * tg);
-    ax[1] = *reinterpret_cast<const uint32_t*>(Xs + (rw + g + 8) * 24 + 2 * tg);
-    ax[2] = *reinterpret_cast<const uint32_t*>(Xs + (rw + g) * 24 + 2 * tg + 8);
-    ax[3] = *reinterpret_cast<const uint32_t*>(Xs + (rw + g + 8) * 24 + 2 * tg + 8);
-#pragma unroll 4
-    for (int nt = 0; nt < 32; ++nt) {
-      float d[4] = {0.f, 0.f, 0.f, 0.f};
-      const int nc = 8 * nt + g;  // B column of this thread
-      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(W1s + nc * 24 + 2 * tg);
-      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(W1s + nc * 24 + 2 * tg + 8);
-      mma_bf16(d, ax, b0, b1);
-      const int c = 8 * nt + 2 * tg;
-      const float h00 = fmaxf(d[0] + bias[c], 0.f), h01 = fmaxf(d[1] + bias[c + 1], 0.f);
-      const float h10 = fmaxf(d[2] + bias[c], 0.f), h11 = fmaxf(d[3] + bias[c + 1], 0.f);
-      *reinterpret_cast<uint32_t*>(H1 + (rw + g) * kHS + c) = pack_bf16(h00, h01);
-      *reinterpret_cast<uint32_t*>(H1 + (rw + g + 8) * kHS + c) = pack_bf16(h10, h11);
-    }
-    __syncwarp();
-    // layers 2 and 3: two halves of 128 hidden units, 16 k-steps each
-    float s_lo = 0.f, s_hi = 0.f;  // rows rw+g and rw+g+8
-#pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      float acc[16][4];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
-#pragma unroll 2
-      for (int ks = 0; ks < 16; ++ks) {
-        const int k0 = 16 * ks;
-        uint32_t ah[4];
-        ah[0] = *reinterpret_cast<const uint32_t*>(H1 + (rw + g) * kHS + k0 + 2 * tg);
-        ah[1] = *reinterpret_cast<const uint32_t*>(H1 + (rw + g + 8) * kHS + k0 + 2 * tg);
-        ah[2] = *reinterpret_cast<const uint32_t*>(H1 + (rw + g) * kHS + k0 + 2 * tg + 8);
-        ah[3] = *reinterpret_cast<const uint32_t*>(H1 + (rw + g + 8) * kHS + k0 + 2 * tg + 8);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int nc = 128 * half + 8 * q + g;
-          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(W2s + nc * kHS + k0 + 2 * tg);
-          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(W2s + nc * kHS + k0 + 2 * tg + 8);
-          mma_bf16(acc[q], ah, b0, b1);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int c = 128 * half + 8 * q + 2 * tg;
-        s_lo += fmaxf(acc[q][0] + bias[256 + c], 0.f) * bias[512 + c] + fmaxf(acc[q][1] + bias[257 + c], 0.f) * bias[513 + c];
-        s_hi += fmaxf(acc[q][2] + bias[256 + c], 0.f) * bias[512 + c] + fmaxf(acc[q][3] + bias[257 + c], 0.f) * bias[513 + c];
-      }
-    }
-    s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 1);
-    s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 2);
-    s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 1);
-    s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 2);
-    if (tg == 0) {
-      if (r0 + rw + g < n) scores[r0 + rw + g] = s_lo + m.b3;
-      if (r0 + rw + g + 8 < n) scores[r0 + rw + g + 8] = s_hi + m.b3;
-    }
-    __syncthreads();  // Xs and H1 are rewritten by the next tile
-  }
-}
-
-__host__ __device__ inline int mlp_smem_bytes() {
-  return (kHidden * kHS + kMlpRows * kHS + kHidden * 24 + kMlpRows * 24) * 2 + 3 * kHidden * 4;
 }
 
 // Stage 2, one block (256 threads) per target: the K best of C candidates by score (higher first,

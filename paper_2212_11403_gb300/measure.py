@@ -4,6 +4,7 @@
     python -m paper_2212_11403_gb300.measure grad    # N=L=10000, gradient over 100 rho intervals
     python -m paper_2212_11403_gb300.measure sparse  # learned sparse path against dense (N=20000) and at N=50000
     python -m paper_2212_11403_gb300.measure table   # ls_forward throughput against Delta-l (N=10000, N=100000)
+    python -m paper_2212_11403_gb300.measure scaling # fused pipeline time against N and against L
 
 CUDA events around each call on the current stream, after one warm-up call; inputs resident in
 device memory.  These are measurements of the library only; the accuracy of each path against the
@@ -259,10 +260,33 @@ def measure_table(big_L=10000):
     return out
 
 
+def measure_scaling():
+    """The paper's scaling experiment (Sec. 5, fig:perfscaling: cost against N and against L) on
+    the dense fused pipeline: time of ls_run_all (forward + backward + distance at 4 loci) over a
+    grid of N at L = 4000 and of L at N = 5000, on the bench workload's generator."""
+    import torch
+    out = []
+    grid = [(N, 4000) for N in (500, 1000, 2000, 5000, 10000, 20000)] + [(5000, L) for L in (500, 1000, 2000, 8000, 16000)]
+    for N, L in grid:
+        w = synth.make_workload("ls_n5000_l20000", N=N, L=L, seed=3000 + N + L)
+        loci = synth.decode_loci(L, 4)
+        ctx = ls.ls_create(w["h"])
+        try:
+            ls.ls_set_params(ctx, w["rho"], w["mu"])
+            d = torch.empty((len(loci), N, N), dtype=torch.float32, device="cuda")
+            t = timed(lambda: ls.ls_run_all(ctx, loci, d, want_pac=False), reps=2)
+        finally:
+            ls.ls_destroy(ctx)
+        cells = float(N) * N * L
+        out.append(dict(workload="ls_n5000_l20000 generator", path="dense fwd+bwd+distance, D = 4", N=N, L=L,
+                        seconds=t, cell_updates_per_s=cells / t, frac_fp32=8 * cells / t / P_FP32))
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["prior", "grad", "sparse", "sparse_case", "table"])
+    ap.add_argument("what", choices=["prior", "grad", "sparse", "sparse_case", "table", "scaling"])
     ap.add_argument("--N", type=int, default=20000, help="sparse_case: haplotypes")
     ap.add_argument("--L", type=int, default=2000, help="sparse_case: loci")
     a = ap.parse_args()
@@ -270,7 +294,8 @@ def main():
     if a.what == "sparse_case":
         recs = measure_sparse_case(a.N, a.L)
     else:
-        recs = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse, table=measure_table)[a.what]()
+        recs = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse, table=measure_table,
+                    scaling=measure_scaling)[a.what]()
     for rec in recs:
         print(json.dumps(rec), flush=True)
 
