@@ -5,6 +5,7 @@
     python -m paper_2212_11403_gb300.measure sparse  # learned sparse path against dense (N=20000) and at N=50000
     python -m paper_2212_11403_gb300.measure table   # ls_forward throughput against Delta-l (N=10000, N=100000)
     python -m paper_2212_11403_gb300.measure scaling # fused pipeline time against N and against L
+    python -m paper_2212_11403_gb300.measure mlp     # the network's tensor-core scorer alone
 
 CUDA events around each call on the current stream, after one warm-up call; inputs resident in
 device memory.  These are measurements of the library only; the accuracy of each path against the
@@ -283,16 +284,38 @@ def measure_scaling():
     return out
 
 
+def measure_mlp(n=1 << 25):
+    """The proposal network's tensor-core scorer alone: ls_mlp_forward on n random feature rows
+    (the call converts the rows to BF16 first, inside the timed region)."""
+    import torch
+    rng = np.random.default_rng(1)
+    p = (rng.normal(0, 1, ls.LS_MLP_PARAMS) * 0.1).astype(np.float32)
+    m = ls.ls_mlp_create(p)
+    try:
+        X = torch.rand((n, 8), device="cuda")
+        X[:, 7] = 0
+        s = torch.empty(n, device="cuda")
+        t = timed(lambda: ls.ls_mlp_forward(m, X, s), reps=3)
+    finally:
+        ls.ls_mlp_destroy(m)
+    flop = 2.0 * n * (7 * 256 + 256 * 256 + 256)
+    return [dict(path="ls_mlp_forward (BF16 tcgen05 scorer)", rows=n, seconds=t, rows_per_s=n / t,
+                 tflops=flop / t / 1e12)]
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["prior", "grad", "sparse", "sparse_case", "table", "scaling"])
+    ap.add_argument("what", choices=["prior", "grad", "sparse", "sparse_case", "table", "scaling", "mlp"])
     ap.add_argument("--N", type=int, default=20000, help="sparse_case: haplotypes")
     ap.add_argument("--L", type=int, default=2000, help="sparse_case: loci")
+    ap.add_argument("--rows", type=int, default=1 << 25, help="mlp: feature rows")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     if a.what == "sparse_case":
         recs = measure_sparse_case(a.N, a.L)
+    elif a.what == "mlp":
+        recs = measure_mlp(a.rows)
     else:
         recs = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse, table=measure_table,
                     scaling=measure_scaling)[a.what]()
