@@ -126,6 +126,26 @@ def test_mlp_inference_and_gradient_match_oracle(ls):
     assert float(np.max(np.abs(g - rg))) <= 1e-4 * float(np.max(np.abs(rg)))
 
 
+def test_mlp_scorer_pipeline_many_tiles_per_cta(ls):
+    """Several 128-row tiles per persistent CTA (the two-accumulator pipeline in steady state), a
+    ragged last tile, and all eight inputs non-zero, against the BF16-rounding network oracle."""
+    import torch
+    rng = np.random.default_rng(17)
+    p = (rng.normal(0, 1, op.N_PARAMS) * 0.15).astype(np.float32)
+    n = 152 * 128 * 3 + 77
+    X = rng.random((n, 8)).astype(np.float32)
+    m = ls.ls_mlp_create(p)
+    try:
+        s = torch.empty(n, dtype=torch.float32, device="cuda")
+        ls.ls_mlp_forward(m, torch.from_numpy(X).cuda(), s)
+        s = s.cpu().numpy().astype(np.float64)
+    finally:
+        ls.ls_mlp_destroy(m)
+    ref16 = op.mlp_forward_bf16(p.astype(np.float64), X.astype(np.float64))
+    scale = float(np.max(np.abs(ref16)))
+    assert float(np.max(np.abs(s - ref16))) <= 2e-3 * scale, float(np.max(np.abs(s - ref16)))
+
+
 def test_mlp_topk_keeps_the_best_scores(ls):
     import torch
     w = synth.make_workload("ls_n50000_l20000", N=120, L=800, seed=23)
