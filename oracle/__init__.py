@@ -65,6 +65,8 @@ def _get():
         lib.lso_run.argtypes = [_U8, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int, _D, _I, ctypes.c_int, _I,
                                 ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int]
         lib.lso_run.restype = ctypes.c_int
+        lib.lso_run_rows.argtypes = lib.lso_run.argtypes
+        lib.lso_run_rows.restype = ctypes.c_int
         lib.lso_grad_target.argtypes = common + [_I, _D, _D]
         lib.lso_grad_target.restype = ctypes.c_double
         lib.lso_pac_grad.argtypes = [_U8, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int, _D, _I, ctypes.c_int, _I,
@@ -164,21 +166,31 @@ def raw_backward_target(h, rho, mu, i, Pi=None):
     return B, G
 
 
-def run(h, rho, mu, loci, targets=None, Pi=None, nthreads=0, want=("post",)):
+def run(h, rho, mu, loci, targets=None, Pi=None, nthreads=0, want=("post",), Pi_rows=None):
     """Forward + backward for `targets` (default: all), results at `loci`.
 
+    The prior is Pi (recipient-major [N, N]), or Pi_rows ([nt, N]: row t = the prior row of
+    recipient targets[t], for N too large for a host matrix), or neither (uniform).
     Returns a dict with the requested keys among alpha, beta, post ([nt, nl, N]), logF, logG
     ([nt, nl]), llf, llb ([nt]).
     """
     h, L, N, rho, mu, Pi = _prep(h, rho, mu, Pi)
     targets = np.arange(N, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
+    fn = _get().lso_run
+    if Pi_rows is not None:
+        if Pi is not None:
+            raise ValueError("give Pi or Pi_rows, not both")
+        Pi = np.ascontiguousarray(Pi_rows, dtype=np.float64)
+        if Pi.shape != (targets.size, N):
+            raise ValueError("Pi_rows must be [len(targets), N]")
+        fn = _get().lso_run_rows
     loci = np.ascontiguousarray(loci, dtype=np.int32)
     nt, nl = targets.size, loci.size
     out = {}
     for key, shape in (("alpha", (nt, nl, N)), ("beta", (nt, nl, N)), ("post", (nt, nl, N)),
                        ("logF", (nt, nl)), ("logG", (nt, nl)), ("llf", (nt,)), ("llb", (nt,))):
         out[key] = np.zeros(shape) if (key in want) else None
-    rc = _get().lso_run(_p(h, _U8), N, L, _p(rho, _D), _p(mu, _D), mu.size, _p(Pi, _D), _p(targets, _I), nt,
+    rc = fn(_p(h, _U8), N, L, _p(rho, _D), _p(mu, _D), mu.size, _p(Pi, _D), _p(targets, _I), nt,
                         _p(loci, _I), nl, _p(out["alpha"], _D), _p(out["beta"], _D), _p(out["post"], _D),
                         _p(out["logF"], _D), _p(out["logG"], _D), _p(out["llf"], _D), _p(out["llb"], _D),
                         int(nthreads))

@@ -39,11 +39,15 @@ static double lso_theta(int hj, int hi, double mu) {
 
 static double lso_mu(const double* mu, int mu_len, int l) { return mu_len == 1 ? mu[0] : mu[l]; }
 
-/* Prior copying probability Pi_ji (Sec. 2.1, Sec. 3.3): uniform 1/(N-1) off the diagonal. */
-static double lso_prior(const double* Pi, int N, int i, int j) {
+/* The prior row of recipient i in a recipient-major Pi (NULL: the uniform prior). */
+static const double* lso_prior_row(const double* Pi, int N, int i) { return Pi ? Pi + (size_t)i * N : NULL; }
+
+/* Prior copying probability Pi_ji (Sec. 2.1, Sec. 3.3) from recipient i's row; uniform 1/(N-1) off
+ * the diagonal when the row is NULL. */
+static double lso_prior(const double* pirow, int N, int i, int j) {
   if (j == i) return 0.0;
-  if (Pi == NULL) return 1.0 / (double)(N - 1);
-  return Pi[(size_t)i * N + j];
+  if (pirow == NULL) return 1.0 / (double)(N - 1);
+  return pirow[j];
 }
 
 /* Eq. rho: rho = 1 - exp(-Ne * m^gamma), evaluated with expm1.  Pinned by the CalcRho values the
@@ -80,8 +84,8 @@ long lso_pack_paper_layout(const uint8_t* h, int N, int L, uint32_t* out) {
  * Returns log F at the last locus = log P(h_i | h_-i) (Sec. 2.1, PAC term).
  * Pinned by brute force, the rho=0 / rho=1 closed forms and the raw recursion below.
  */
-double lso_forward_target(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
-                          const double* Pi, int i, const int* slot, double* alpha_out, double* logF_out) {
+static double lso_forward_row(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
+                              const double* pirow, int i, const int* slot, double* alpha_out, double* logF_out) {
   double* a = (double*)malloc(sizeof(double) * N);
   double* b = (double*)malloc(sizeof(double) * N);
   double logF = 0.0;
@@ -89,13 +93,13 @@ double lso_forward_target(const uint8_t* h, int N, int L, const double* rho, con
     const uint8_t* hl = h + (size_t)l * N;
     double m = lso_mu(mu, mu_len, l);
     if (l == 0) {
-      for (int j = 0; j < N; ++j) b[j] = lso_theta(hl[j], hl[i], m) * lso_prior(Pi, N, i, j);
+      for (int j = 0; j < N; ++j) b[j] = lso_theta(hl[j], hl[i], m) * lso_prior(pirow, N, i, j);
     } else {
       double s = 0.0;
       for (int j = 0; j < N; ++j) s += a[j];
       double r = rho[l - 1];
       for (int j = 0; j < N; ++j)
-        b[j] = lso_theta(hl[j], hl[i], m) * ((1.0 - r) * a[j] / s + r * lso_prior(Pi, N, i, j));
+        b[j] = lso_theta(hl[j], hl[i], m) * ((1.0 - r) * a[j] / s + r * lso_prior(pirow, N, i, j));
     }
     b[i] = 0.0; /* pi_ii = 0 makes alpha_ii identically zero */
     double s_new = 0.0;
@@ -123,8 +127,8 @@ double lso_forward_target(const uint8_t* h, int N, int L, const double* rho, con
  * Returns log G^0-ish likelihood: log G at locus 0 + log sum_j beta^0_j theta^0_j pi_j, which
  * equals log P(h_i | h_-i).  Pinned by forward/backward likelihood agreement and brute force.
  */
-double lso_backward_target(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
-                           const double* Pi, int i, const int* slot, double* beta_out, double* logG_out) {
+static double lso_backward_row(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
+                               const double* pirow, int i, const int* slot, double* beta_out, double* logG_out) {
   double* bt = (double*)malloc(sizeof(double) * N);
   double* nb = (double*)malloc(sizeof(double) * N);
   double logG = 0.0;
@@ -135,7 +139,7 @@ double lso_backward_target(const uint8_t* h, int N, int L, const double* rho, co
       double m1 = lso_mu(mu, mu_len, l + 1);
       double S = 0.0;
       for (int j = 0; j < N; ++j)
-        if (j != i) S += bt[j] * lso_theta(h1[j], h1[i], m1) * lso_prior(Pi, N, i, j);
+        if (j != i) S += bt[j] * lso_theta(h1[j], h1[i], m1) * lso_prior(pirow, N, i, j);
       double r = rho[l];
       for (int j = 0; j < N; ++j) nb[j] = (1.0 - r) * bt[j] * lso_theta(h1[j], h1[i], m1) / S + r;
       logG += log(S);
@@ -154,7 +158,7 @@ double lso_backward_target(const uint8_t* h, int N, int L, const double* rho, co
   double m0 = lso_mu(mu, mu_len, 0);
   double S0 = 0.0;
   for (int j = 0; j < N; ++j)
-    if (j != i) S0 += bt[j] * lso_theta(h0[j], h0[i], m0) * lso_prior(Pi, N, i, j);
+    if (j != i) S0 += bt[j] * lso_theta(h0[j], h0[i], m0) * lso_prior(pirow, N, i, j);
   free(bt);
   free(nb);
   return logG + log(S0);
@@ -184,6 +188,16 @@ double lso_distance_pair(double p_ji, double p_ij) {
   return -(log(a) + log(b)) / 2.0;
 }
 
+double lso_forward_target(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
+                          const double* Pi, int i, const int* slot, double* alpha_out, double* logF_out) {
+  return lso_forward_row(h, N, L, rho, mu, mu_len, lso_prior_row(Pi, N, i), i, slot, alpha_out, logF_out);
+}
+
+double lso_backward_target(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
+                           const double* Pi, int i, const int* slot, double* beta_out, double* logG_out) {
+  return lso_backward_row(h, N, L, rho, mu, mu_len, lso_prior_row(Pi, N, i), i, slot, beta_out, logG_out);
+}
+
 /*
  * Raw (unscaled) recursions, Eq. raw_forward / raw_backward with F, G of Eq. F / Eq. G, for
  * tiny L only (no rescaling, so they underflow on long inputs).  Used to pin the rescaled
@@ -192,11 +206,12 @@ double lso_distance_pair(double p_ji, double p_ij) {
  */
 void lso_raw_forward_target(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
                             const double* Pi, int i, double* alpha_t, double* F) {
+  const double* pirow = lso_prior_row(Pi, N, i);
   for (int l = 0; l < L; ++l) {
     const uint8_t* hl = h + (size_t)l * N;
     double m = lso_mu(mu, mu_len, l);
     for (int j = 0; j < N; ++j) {
-      double pij = lso_prior(Pi, N, i, j);
+      double pij = lso_prior(pirow, N, i, j);
       if (l == 0) alpha_t[j] = lso_theta(hl[j], hl[i], m) * pij;
       else
         alpha_t[(size_t)l * N + j] = lso_theta(hl[j], hl[i], m) *
@@ -209,6 +224,7 @@ void lso_raw_forward_target(const uint8_t* h, int N, int L, const double* rho, c
 
 void lso_raw_backward_target(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
                              const double* Pi, int i, double* beta_t, double* G) {
+  const double* pirow = lso_prior_row(Pi, N, i);
   for (int j = 0; j < N; ++j) beta_t[(size_t)(L - 1) * N + j] = 1.0;
   G[L - 1] = 1.0;
   for (int l = L - 2; l >= 0; --l) {
@@ -216,7 +232,7 @@ void lso_raw_backward_target(const uint8_t* h, int N, int L, const double* rho, 
     double m1 = lso_mu(mu, mu_len, l + 1);
     double g = 0.0;
     for (int j = 0; j < N; ++j)
-      g += beta_t[(size_t)(l + 1) * N + j] * lso_theta(h1[j], h1[i], m1) * lso_prior(Pi, N, i, j);
+      g += beta_t[(size_t)(l + 1) * N + j] * lso_theta(h1[j], h1[i], m1) * lso_prior(pirow, N, i, j);
     G[l] = g;
     for (int j = 0; j < N; ++j)
       beta_t[(size_t)l * N + j] = (1.0 - rho[l]) * beta_t[(size_t)(l + 1) * N + j] * lso_theta(h1[j], h1[i], m1) + rho[l] * g;
@@ -229,9 +245,10 @@ void lso_raw_backward_target(const uint8_t* h, int N, int L, const double* rho, 
  *   alpha, beta, post : [nt][nl][N]      logF, logG : [nt][nl]      llf, llb : [nt]
  * OpenMP over targets (each target is an independent HMM, Sec. 3.7.1).
  */
-int lso_run(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len, const double* Pi,
-            const int* targets, int nt, const int* loci, int nl, double* alpha, double* beta, double* post,
-            double* logF, double* logG, double* llf, double* llb, int nthreads) {
+static int lso_run_impl(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
+                        const double* Pi, int pi_rows, const int* targets, int nt, const int* loci, int nl,
+                        double* alpha, double* beta, double* post, double* logF, double* logG, double* llf,
+                        double* llb, int nthreads) {
   if (N < 2 || L < 1 || nt < 0 || nl < 0) return -1;
   for (int k = 0; k < nl; ++k)
     if (loci[k] < 0 || loci[k] >= L) return -1;
@@ -254,8 +271,9 @@ int lso_run(const uint8_t* h, int N, int L, const double* rho, const double* mu,
     for (int t = 0; t < nt; ++t) {
       int i = targets[t];
       if (i < 0 || i >= N) { err = -1; continue; }
-      double f = lso_forward_target(h, N, L, rho, mu, mu_len, Pi, i, slot, A, lF);
-      double b = lso_backward_target(h, N, L, rho, mu, mu_len, Pi, i, slot, B, lG);
+      const double* pirow = pi_rows ? (Pi ? Pi + (size_t)t * N : NULL) : lso_prior_row(Pi, N, i);
+      double f = lso_forward_row(h, N, L, rho, mu, mu_len, pirow, i, slot, A, lF);
+      double b = lso_backward_row(h, N, L, rho, mu, mu_len, pirow, i, slot, B, lG);
       for (int k = 0; k < nl; ++k) {
         /* a locus may be requested twice: copy from the slot that was filled */
         int s = slot[loci[k]];
@@ -275,6 +293,22 @@ int lso_run(const uint8_t* h, int N, int L, const double* rho, const double* mu,
     free(lG);
   }
   return err;
+}
+
+int lso_run(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len, const double* Pi,
+            const int* targets, int nt, const int* loci, int nl, double* alpha, double* beta, double* post,
+            double* logF, double* logG, double* llf, double* llb, int nthreads) {
+  return lso_run_impl(h, N, L, rho, mu, mu_len, Pi, 0, targets, nt, loci, nl, alpha, beta, post, logF, logG, llf, llb,
+                      nthreads);
+}
+
+/* The same with only the targets' prior rows: Pi_rows[t*N + j] = Pi_{j, targets[t]} (recipient-major
+ * rows, diagonal entry ignored), so that large N needs no N x N host matrix. */
+int lso_run_rows(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
+                 const double* Pi_rows, const int* targets, int nt, const int* loci, int nl, double* alpha,
+                 double* beta, double* post, double* logF, double* logG, double* llf, double* llb, int nthreads) {
+  return lso_run_impl(h, N, L, rho, mu, mu_len, Pi_rows, 1, targets, nt, loci, nl, alpha, beta, post, logF, logG, llf,
+                      llb, nthreads);
 }
 
 /*
@@ -305,6 +339,7 @@ void lso_distance_block(const double* post, const int* targets, int nt, int N, d
  */
 double lso_grad_target(const uint8_t* h, int N, int L, const double* rho, const double* mu, int mu_len,
                        const double* Pi, int i, const int* interval_of, double* dlogmu, double* dlogrho) {
+  const double* pirow = lso_prior_row(Pi, N, i);
   double* A = (double*)malloc(sizeof(double) * (size_t)L * N); /* normalised alpha^l */
   double* a = (double*)malloc(sizeof(double) * N);
   double* b = (double*)malloc(sizeof(double) * N);
@@ -313,10 +348,10 @@ double lso_grad_target(const uint8_t* h, int N, int L, const double* rho, const 
     const uint8_t* hl = h + (size_t)l * N;
     double m = lso_mu(mu, mu_len, l);
     if (l == 0) {
-      for (int j = 0; j < N; ++j) b[j] = lso_theta(hl[j], hl[i], m) * lso_prior(Pi, N, i, j);
+      for (int j = 0; j < N; ++j) b[j] = lso_theta(hl[j], hl[i], m) * lso_prior(pirow, N, i, j);
     } else {
       double r = rho[l - 1];
-      for (int j = 0; j < N; ++j) b[j] = lso_theta(hl[j], hl[i], m) * ((1.0 - r) * a[j] + r * lso_prior(Pi, N, i, j));
+      for (int j = 0; j < N; ++j) b[j] = lso_theta(hl[j], hl[i], m) * ((1.0 - r) * a[j] + r * lso_prior(pirow, N, i, j));
     }
     b[i] = 0.0;
     double s = 0.0;
@@ -348,7 +383,7 @@ double lso_grad_target(const uint8_t* h, int N, int L, const double* rho, const 
       int mm = l - 1; /* interval between loci l-1 and l */
       double S = 0.0;
       for (int j = 0; j < N; ++j)
-        if (j != i) S += bt[j] * lso_theta(hl[j], hl[i], m) * lso_prior(Pi, N, i, j);
+        if (j != i) S += bt[j] * lso_theta(hl[j], hl[i], m) * lso_prior(pirow, N, i, j);
       double Am = 0.0;
       for (int j = 0; j < N; ++j)
         if (j != i) Am += A[(size_t)mm * N + j] * lso_theta(hl[j], hl[i], m) * bt[j] / S;

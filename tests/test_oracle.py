@@ -111,6 +111,25 @@ def test_oracle_matches_brute_force(seed, N, L):
         np.testing.assert_allclose(res["post"][i], marg, rtol=1e-10, atol=1e-14)
 
 
+def test_prior_rows_form_equals_the_matrix_form():
+    """oracle.run with only the targets' prior rows (for N too large for a host matrix) gives the
+    same results as with the full matrix, bit for bit, and with a row permuted it does not."""
+    rng = np.random.default_rng(12)
+    N, L = 11, 30
+    inst = synth.random_tiny(rng, N, L, mu_kind="vector", pi_kind="matrix")
+    h, rho, mu, Pi = inst["h"], inst["rho"], inst["mu"], inst["Pi"]
+    targets = np.array([7, 0, 3, 10])
+    loci = [0, 13, L - 1]
+    want = ("alpha", "beta", "post", "logF", "logG", "llf", "llb")
+    full = oracle.run(h, rho, mu, loci, targets=targets, Pi=Pi, want=want)
+    rows = oracle.run(h, rho, mu, loci, targets=targets, Pi_rows=Pi[targets], want=want)
+    for k in want:
+        np.testing.assert_array_equal(rows[k], full[k])
+    swapped = Pi[targets][[1, 0, 2, 3]]
+    other = oracle.run(h, rho, mu, loci, targets=targets, Pi_rows=swapped, want=("llf",))
+    assert abs(other["llf"][0] - full["llf"][0]) > 1e-9
+
+
 # ---------------------------------------------------------------- raw vs rescaled recursions
 @pytest.mark.parametrize("pi_kind", ["uniform", "matrix"])
 def test_rescaled_equals_raw(pi_kind):
