@@ -107,6 +107,19 @@ int ls_calc_rho(const double* m, int32_t n, double Ne, double gamma, double* rho
 int ls_set_params(ls_ctx* ctx, const double* rho, const double* mu, int32_t mu_len, const float* Pi,
                   uint64_t* hash_out);
 
+/* Storage format of a prior matrix (an option of this library; the paper's Pi is double).
+ * LS_PRIOR_FP32 (the default): Pi as the caller's FP32 values.  LS_PRIOR_BF16: ls_set_params
+ * rounds every entry of its copy of Pi to the nearest bfloat16 (ties to even) after validating
+ * the caller's values, and all kernels then run with the rounded prior, whose rows sum to 1 only
+ * within about 2^-9 per entry; the results are those of the rounded matrix.  A target's prior row
+ * then fits on chip next to its state for N > 20480 (the large-N kernels keep it in shared memory
+ * as bfloat16): a prior matrix with N in (20480, 106496] needs this format (LS_ERR_UNSUPPORTED from
+ * the propagation calls otherwise).  Takes effect at the next ls_set_params and enters the
+ * parameter fingerprint.  LS_ERR_ARG for another value. */
+#define LS_PRIOR_FP32 0
+#define LS_PRIOR_BF16 1
+int ls_set_prior_format(ls_ctx* ctx, int32_t format);
+
 /* ---- forward / backward tables (Sec. 3.4-3.5, Table tab:fwdbck) ----------------------------- */
 
 /* Create a table (kind LS_FWD or LS_BWD) for targets [t_from, t_to), 0 <= t_from < t_to <= N.

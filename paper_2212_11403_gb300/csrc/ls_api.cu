@@ -30,6 +30,8 @@ void ls_register_group10(std::vector<PropKernelInfo>& out);
 void ls_register_group11(std::vector<PropKernelInfo>& out);
 void ls_register_group12(std::vector<PropKernelInfo>& out);
 void ls_register_group13(std::vector<PropKernelInfo>& out);
+void ls_register_group14(std::vector<PropKernelInfo>& out);
+void ls_register_group15(std::vector<PropKernelInfo>& out);
 
 namespace {
 
@@ -69,6 +71,8 @@ std::vector<PropKernelInfo>& registry() {
     ls_register_group11(v);
     ls_register_group12(v);
     ls_register_group13(v);
+    ls_register_group14(v);
+    ls_register_group15(v);
   });
   return v;
 }
@@ -122,6 +126,7 @@ int candidates(ls_ctx* c, Cand* out, int* nout) {
   for (const auto& k : registry()) {
     if (*nout >= kMaxCand) break;
     if (k.st != 0 || k.pim != pim || !k.serves(N)) continue;
+    if (k.pi16 && !c->prior_bf16) continue;  // holds the prior as bfloat16: only for the BF16 format
     if (pin && !(k.tpw == pa && k.w == pb && k.kq == pk)) continue;
     const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;
@@ -138,6 +143,8 @@ int candidates(ls_ctx* c, Cand* out, int* nout) {
   }
   if (*nout == 0) {
     if (pin) return fail(LS_ERR_UNSUPPORTED, "LS_PROP_VARIANT=%s does not serve N=%d", ov, N);
+    if (pim && !c->prior_bf16 && N > 20480)
+      return fail(LS_ERR_UNSUPPORTED, "a prior matrix at N=%d > 20480 needs the BF16 prior format (ls_set_prior_format)", N);
     return fail(LS_ERR_UNSUPPORTED, "no compiled propagation variant serves N=%d", N);
   }
   return LS_OK;
@@ -468,6 +475,14 @@ int ls_calc_rho(const double* m, int32_t n, double Ne, double gamma, double* rho
   return LS_OK;
 }
 
+int ls_set_prior_format(ls_ctx* ctx, int32_t format) {
+  int rc = check_ctx(ctx);
+  if (rc) return rc;
+  if (format != LS_PRIOR_FP32 && format != LS_PRIOR_BF16) return fail(LS_ERR_ARG, "unknown prior format %d", format);
+  ctx->prior_bf16 = format == LS_PRIOR_BF16 ? 1 : 0;
+  return LS_OK;
+}
+
 int ls_set_params(ls_ctx* ctx, const double* rho, const double* mu, int32_t mu_len, const float* Pi, uint64_t* hash_out) {
   int rc = check_ctx(ctx);
   if (rc) return rc;
@@ -484,22 +499,32 @@ int ls_set_params(ls_ctx* ctx, const double* rho, const double* mu, int32_t mu_l
   if (L > 1) h = fnv1a(h, rho, sizeof(double) * (L - 1));
   h = fnv1a(h, &mu_len, sizeof mu_len);
   h = fnv1a(h, mu, sizeof(double) * mu_len);
-  std::vector<float> pih;
   if (Pi) {
+    // validated and fingerprinted on the GPU (one CTA per row); the host reads three words per row
     if (!is_device_ptr(Pi)) return fail(LS_ERR_ARG, "Pi must be device memory");
-    pih.resize((size_t)N * N);
-    CUDA_TRY(cudaMemcpy(pih.data(), Pi, sizeof(float) * pih.size(), cudaMemcpyDeviceToHost));
+    void* chk = nullptr;
+    const size_t bad_bytes = (((size_t)N * sizeof(int) + 7) / 8) * 8;  // the doubles start 8-byte aligned
+    if ((rc = dev_alloc(nullptr, &chk, bad_bytes + (size_t)N * (sizeof(double) + sizeof(uint64_t))))) return rc;
+    int* bad = static_cast<int*>(chk);
+    double* sums = reinterpret_cast<double*>(static_cast<char*>(chk) + bad_bytes);
+    unsigned long long* hs = reinterpret_cast<unsigned long long*>(sums + N);
+    std::vector<int> bh(N);
+    std::vector<double> sh(N);
+    std::vector<unsigned long long> hh(N);
+    lsk::prior_check_kernel<<<N, 256>>>(Pi, N, bad, sums, hs);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(bh.data(), bad, sizeof(int) * N, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(sh.data(), sums, sizeof(double) * N, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hh.data(), hs, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost);
+    cudaFree(chk);
+    if (e != cudaSuccess) return fail(LS_ERR_CUDA, "checking the prior: %s", cudaGetErrorString(e));
     for (int i = 0; i < N; ++i) {
-      double s = 0.0;
-      for (int j = 0; j < N; ++j) {
-        const float v = pih[(size_t)i * N + j];
-        if (!(v >= 0.0f) || !std::isfinite(v)) return fail(LS_ERR_ARG, "Pi[%d][%d] = %g is not a probability", i, j, v);
-        s += v;
-      }
-      if (pih[(size_t)i * N + i] != 0.0f) return fail(LS_ERR_ARG, "Pi[%d][%d] must be 0 (Sec. 2.1)", i, i);
-      if (std::fabs(s - 1.0) > 1e-5) return fail(LS_ERR_ARG, "prior row %d sums to %.9g, not 1", i, s);
+      if (bh[i] & 1) return fail(LS_ERR_ARG, "prior row %d holds a negative or non-finite entry", i);
+      if (bh[i] & 2) return fail(LS_ERR_ARG, "Pi[%d][%d] must be 0 (Sec. 2.1)", i, i);
+      if (std::fabs(sh[i] - 1.0) > 1e-5) return fail(LS_ERR_ARG, "prior row %d sums to %.9g, not 1", i, sh[i]);
     }
-    h = fnv1a(h, pih.data(), sizeof(float) * pih.size());
+    h = fnv1a(h, hh.data(), sizeof(unsigned long long) * hh.size());
+    h = fnv1a(h, &ctx->prior_bf16, sizeof ctx->prior_bf16);
   }
   // per-locus FP32 constants, rounded once from double
   std::vector<float> omr(std::max(L - 1, 1)), rrf(std::max(L - 1, 1)), rrb(std::max(L - 1, 1)), thm(L), thx(L);
@@ -528,6 +553,12 @@ int ls_set_params(ls_ctx* ctx, const double* rho, const double* mu, int32_t mu_l
   if (Pi) {
     if (!ctx->Pi && (rc = dev_alloc(ctx, (void**)&ctx->Pi, sizeof(float) * (size_t)N * N))) return rc;
     CUDA_TRY(cudaMemcpy(ctx->Pi, Pi, sizeof(float) * (size_t)N * N, cudaMemcpyDeviceToDevice));
+    if (ctx->prior_bf16) {
+      const long long n = (long long)N * N;
+      lsk::prior_bf16_kernel<<<(unsigned)((n + 255) / 256), 256>>>(ctx->Pi, n);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaDeviceSynchronize());
+    }
   } else if (ctx->Pi) {
     cudaFree(ctx->Pi);
     ctx->bytes -= sizeof(float) * (size_t)N * N;

@@ -3,12 +3,68 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "ls_prop.cuh"
 
 namespace lsk {
+
+// Validation and fingerprint of a prior matrix (Sec. 2.1: Pi, recipient-major rows that sum to one
+// with a zero diagonal), one CTA of 256 threads per row.  bad[i]: bit 0 a negative or non-finite
+// entry, bit 1 a non-zero diagonal; sums[i]: the row sum in FP64 (thread-strided partial sums,
+// added in thread order); hashes[i]: FNV-1a of each thread's entries' bytes in column order, the
+// 256 thread hashes folded in thread order.  Deterministic for a given matrix.
+__global__ void prior_check_kernel(const float* __restrict__ Pi, int N, int* __restrict__ bad,
+                                   double* __restrict__ sums, unsigned long long* __restrict__ hashes) {
+  __shared__ double ps[256];
+  __shared__ unsigned long long ph[256];
+  __shared__ int pb;
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const float* row = Pi + (size_t)i * N;
+  if (tid == 0) pb = 0;
+  __syncthreads();
+  int b = 0;
+  double s = 0.0;
+  unsigned long long h = 1469598103934665603ull;
+  for (int j = tid; j < N; j += 256) {
+    const float v = row[j];
+    if (!(v >= 0.0f) || !isfinite(v)) b |= 1;
+    s += (double)v;
+    const uint32_t u = __float_as_uint(v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      h ^= (u >> (8 * k)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  }
+  if (tid == 0 && row[i] != 0.0f) b |= 2;
+  if (b) atomicOr(&pb, b);
+  ps[tid] = s;
+  ph[tid] = h;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    unsigned long long g = 1469598103934665603ull;
+    for (int k = 0; k < 256; ++k) {
+      t += ps[k];
+      for (int q = 0; q < 8; ++q) {
+        g ^= (ph[k] >> (8 * q)) & 0xffull;
+        g *= 1099511628211ull;
+      }
+    }
+    bad[i] = pb;
+    sums[i] = t;
+    hashes[i] = g;
+  }
+}
+
+// The BF16 prior format: every entry rounded to the nearest bfloat16 (ties to even), in place.
+__global__ void prior_bf16_kernel(float* __restrict__ Pi, long long n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) Pi[e] = __bfloat162float(__float2bfloat16_rn(Pi[e]));
+}
 
 // Doubled rows for the propagation kernel: out[l][q] holds bits [32q, 32q+32) of the cyclic string
 // b -> h[l][b mod N] for b < 2N (zero beyond), so every rotated slice is one contiguous run.

@@ -1,5 +1,5 @@
-// ls_hyb.cuh -- dense propagation for large N (uniform prior): one target per CTA of 512 threads,
-// the target's state split between registers and shared memory.
+// ls_hyb.cuh -- dense propagation for large N: one target per CTA of 512 threads, the target's
+// state split between registers and shared memory.
 //
 // Thread t owns donor positions [B t, B (t+1)), B = 4 (QR + QS): its first QR quads of 4 cells stay
 // in registers for all loci, the other QS quads sit in shared memory in quad-major order
@@ -22,7 +22,18 @@
 // every warp writes its partial sum into both CTAs' shared memory (distributed shared memory), one
 // cluster barrier publishes them, and both CTAs add the 32 partials in the same fixed order, so they
 // hold bit-identical normalisers.
+//
+// Prior matrix (PIM = 1, Sec. 2.1 copying prior Pi): the target's prior row stays on chip for all
+// loci as bfloat16, four values per 8 bytes in the same quad-major order ([Q][512] in shared
+// memory, 8 bytes per position quad), which is why these variants need the BF16 prior format (the
+// context rounds Pi once, so the conversion here is exact).  The forward adds rho * pi_j per cell
+// (one more multiply), the backward normaliser is sum_j pi_j t_j (an FMA in place of the add);
+// padding and the target's own position have pi = 0, so no junk correction is needed.  The
+// register quads are staged through no shared memory: at stores every thread writes its own
+// positions.
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include "ls_prop.cuh"
 
@@ -48,36 +59,41 @@ __device__ __forceinline__ void st_cluster(float* local, uint32_t rank, float v)
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
 }
 
-template <int QS>
+constexpr int kHybPimMaxN1 = kHybThreads * 4 * (kHybQR + 14);  // largest N of one CTA with a prior matrix
+
+template <int QS, int PIM = 0>
 struct HybCfg {
   static constexpr int Q = kHybQR + QS;       // quads per thread
   static constexpr int B = 4 * Q;             // positions per thread
   static constexpr int NP = kHybThreads * B;  // positions per target (N <= NP)
   static constexpr int NWA = (B + 31) / 32;   // aligned match words per thread
   static constexpr int NW = NWA + 1;          // row words read per thread (funnel shift)
-  // dynamic shared memory: the QS shared quads [QS][512], staging of the register quads at store
-  // loci [QR][512] (float4 each), two buffers of 16 warp partials
+  // dynamic shared memory: the QS shared quads [QS][512] (float4 each); with a prior matrix the
+  // prior quads [Q][512] (4 x bf16 each), else the staging of the register quads at store loci
+  // [QR][512] (float4 each); two buffers of 32 warp partials
   static constexpr int XS_OFF = 0;
-  static constexpr int STG_OFF = XS_OFF + QS * kHybThreads * 16;
-  static constexpr int PART_OFF = STG_OFF + kHybQR * kHybThreads * 16;
+  static constexpr int PS_OFF = XS_OFF + QS * kHybThreads * 16;
+  static constexpr int STG_OFF = PS_OFF + (PIM ? Q * kHybThreads * 8 : 0);
+  static constexpr int PART_OFF = STG_OFF + (PIM ? 0 : kHybQR * kHybThreads * 16);
   static constexpr int BYTES = PART_OFF + 2 * 32 * 4;
   __host__ __device__ static int smem_bytes() { return BYTES; }
   // beyond the register-tile kernels' range (N <= 20480); with CL CTAs per target, beyond the
-  // one-CTA range (N <= 57344)
+  // one-CTA range (N <= 57344; with a prior matrix N <= 53248)
   __host__ __device__ static bool serves(int N, int CL = 1) {
-    return CL == 1 ? (N > 20480 && N <= NP) : (N > 57344 && N <= CL * NP);
+    return CL == 1 ? (N > 20480 && N <= NP) : (N > (PIM ? kHybPimMaxN1 : 57344) && N <= CL * NP);
   }
 };
 
-template <int DIR, int QS, int CL>
+template <int DIR, int QS, int CL, int PIM = 0>
 __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams p) {
   static_assert(CL == 1 || CL == 2, "one CTA or a cluster of two per target");
-  using C = HybCfg<QS>;
+  using C = HybCfg<QS, PIM>;
   constexpr int QR = kHybQR, Q = C::Q, B = C::B, NWA = C::NWA, NW = C::NW, T = kHybThreads;
   constexpr int step_dir = DIR == 0 ? 1 : -1;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* Xs = reinterpret_cast<float4*>(smem + C::XS_OFF);    // [QS][T] shared quads
   float4* Stg = reinterpret_cast<float4*>(smem + C::STG_OFF);  // [QR][T] register quads at stores
+  uint2* Ps = reinterpret_cast<uint2*>(smem + C::PS_OFF);      // [Q][T] prior quads (PIM)
   float* part = reinterpret_cast<float*>(smem + C::PART_OFF);  // [2][32]
   const int N = p.N, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rank = CL == 2 ? (int)cluster_rank() : 0;
@@ -103,6 +119,18 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     }
     vm[k] = m;
   }
+  if (PIM) {  // this thread's prior values as bfloat16 pairs (0 on padding and on the target)
+    const float* prow = p.Pi + (size_t)tgt * N;
+    for (int q = 0; q < Q; ++q) {
+      uint32_t hb[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int pos = d0 + 4 * q + e;
+        hb[e] = __bfloat16_as_ushort(__float2bfloat16_rn((pos < N && pos != tgt) ? prow[pos] : 0.0f));
+      }
+      Ps[q * T + tid] = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+    }
+  }
 
   // element e of quad q of thread t: shared or staged location (quad-major)
   auto elem = [&](int q, int t, int e) -> float* {
@@ -113,7 +141,19 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   f2 x[QR][2];
 #pragma unroll
   for (int q = 0; q < QR; ++q) x[q][0] = x[q][1] = make_float2(0.f, 0.f);
-  if (p.load_state) {
+  if (p.load_state && PIM) {  // every thread reads its own positions
+    auto ld = [&](int pos) -> float { return (pos < N && pos != tgt) ? p.state[(size_t)row * N + pos] : 0.0f; };
+#pragma unroll
+    for (int q = 0; q < QR; ++q) {
+      x[q][0] = make_float2(ld(d0 + 4 * q), ld(d0 + 4 * q + 1));
+      x[q][1] = make_float2(ld(d0 + 4 * q + 2), ld(d0 + 4 * q + 3));
+    }
+    for (int q = QR; q < Q; ++q) {
+      const int b4 = d0 + 4 * q;
+      Xs[(q - QR) * T + tid] = make_float4(ld(b4), ld(b4 + 1), ld(b4 + 2), ld(b4 + 3));
+    }
+    __syncthreads();
+  } else if (p.load_state) {
     for (int i = tid; i < C::NP; i += T) {
       const int t = i / B, o = i - t * B, g = pos0 + i;
       *elem(o >> 2, t, o & 3) = (g < N && g != tgt) ? p.state[(size_t)row * N + g] : 0.0f;
@@ -155,6 +195,31 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   };
   // store the row (x, or c x + r when affine) to w1 / multiply m1 by it / w2 (any may be null)
   auto store_state = [&](float* w1, float* m1, float* w2, bool affine, float c, float r) {
+    if (PIM) {  // every thread writes its own positions
+      auto put = [&](int pos, float xv) {
+        if (pos >= N) return;
+        const float v = pos == tgt ? 0.0f : (affine ? fmaf(c, xv, r) : xv);
+        const size_t ro = (size_t)row * N + pos;
+        if (w1) w1[ro] = v;
+        if (m1) m1[ro] = pos == tgt ? 0.0f : m1[ro] * (v * kProdScale);
+        if (w2) w2[ro] = v;
+      };
+#pragma unroll
+      for (int q = 0; q < QR; ++q) {
+        put(d0 + 4 * q, x[q][0].x);
+        put(d0 + 4 * q + 1, x[q][0].y);
+        put(d0 + 4 * q + 2, x[q][1].x);
+        put(d0 + 4 * q + 3, x[q][1].y);
+      }
+      for (int q = QR; q < Q; ++q) {
+        const float4 v = Xs[(q - QR) * T + tid];
+        put(d0 + 4 * q, v.x);
+        put(d0 + 4 * q + 1, v.y);
+        put(d0 + 4 * q + 2, v.z);
+        put(d0 + 4 * q + 3, v.w);
+      }
+      return;
+    }
 #pragma unroll
     for (int q = 0; q < QR; ++q) Stg[q * T + tid] = make_float4(x[q][0].x, x[q][0].y, x[q][1].x, x[q][1].y);
     __syncthreads();
@@ -219,7 +284,7 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     const int mi = DIR == 0 ? l - 1 : l;
     if (step == 0 && p.init) {
       c = 0.0f;
-      r = DIR == 0 ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
+      r = (DIR == 0 && !PIM) ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
     } else if (step == 0 && DIR == 1) {
       c = 1.0f;  // backward resume: x = theta^l beta^l from the stored beta
       r = 0.0f;
@@ -272,19 +337,31 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     for (int q = 0; q < Q; ++q) {
       const uint32_t w = aw[(4 * q) >> 5];
       const int b = (4 * q) & 31;
+      f2 p01 = make_float2(0.f, 0.f), p23 = make_float2(0.f, 0.f);
+      if (PIM) {  // the prior quad, bfloat16 -> FP32 (exact)
+        const uint2 pb = Ps[q * T + tid];
+        p01 = make_float2(__uint_as_float(pb.x << 16), __uint_as_float(pb.x & 0xffff0000u));
+        p23 = make_float2(__uint_as_float(pb.y << 16), __uint_as_float(pb.y & 0xffff0000u));
+      }
+      // u = c x + r (forward with a prior matrix: c x + r pi_j)
+      auto pre = [&](f2 xv, f2 pv) -> f2 {
+        return (PIM && DIR == 0) ? __ffma2_rn(C2, xv, __fmul2_rn(R2, pv)) : __ffma2_rn(C2, xv, R2);
+      };
+      // the normaliser: sum_j x_j (backward with a prior matrix: sum_j pi_j t_j)
+      auto add = [&](f2 a, f2 y, f2 pv) -> f2 { return (PIM && DIR == 1) ? __ffma2_rn(y, pv, a) : __fadd2_rn(a, y); };
       if (q < QR) {
         const int qr = q < QR ? q : 0;
-        emit(__ffma2_rn(C2, x[qr][0], R2), __ffma2_rn(C2, x[qr][1], R2), w, b, x[qr][0], x[qr][1]);
-        acc0 = __fadd2_rn(acc0, x[qr][0]);
-        acc1 = __fadd2_rn(acc1, x[qr][1]);
+        emit(pre(x[qr][0], p01), pre(x[qr][1], p23), w, b, x[qr][0], x[qr][1]);
+        acc0 = add(acc0, x[qr][0], p01);
+        acc1 = add(acc1, x[qr][1], p23);
       } else {
         float4* sp = Xs + (q - QR) * T + tid;
         const float4 v = *sp;
         f2 y01, y23;
-        emit(__ffma2_rn(C2, make_float2(v.x, v.y), R2), __ffma2_rn(C2, make_float2(v.z, v.w), R2), w, b, y01, y23);
+        emit(pre(make_float2(v.x, v.y), p01), pre(make_float2(v.z, v.w), p23), w, b, y01, y23);
         *sp = make_float4(y01.x, y01.y, y23.x, y23.y);
-        acc0 = __fadd2_rn(acc0, y01);
-        acc1 = __fadd2_rn(acc1, y23);
+        acc0 = add(acc0, y01, p01);
+        acc1 = add(acc1, y23, p23);
       }
     }
     xs = __fmul_rn(u_ratio, __fmaf_rn(cu, xs, ru));  // junk positions: always the "small" factor
@@ -299,8 +376,8 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
       ++store_next;
       next_store_l = store_next < p.n_store ? p.store_loci[store_next] : -1;
     }
-    float sig = reduce((acc0.x + acc0.y) + (acc1.x + acc1.y), step & 1) - n_junk * xs;
-    if (DIR == 1) sig *= p.pi_u;
+    float sig = reduce((acc0.x + acc0.y) + (acc1.x + acc1.y), step & 1) - (PIM ? 0.0f : n_junk * xs);
+    if (DIR == 1 && !PIM) sig *= p.pi_u;
     if (tid == 0) {
       const float sg = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
       if (sg < 1.17549435e-38f) sts |= 1u;      // LS_STATUS_UNDERFLOW

@@ -19,6 +19,7 @@ struct PropKernelInfo {
   int (*smem_bytes)(int rw2);
   bool (*serves)(int N);
   int cpt = 1;  // CTAs per target (2: a thread-block cluster of two CTAs shares one target)
+  int pi16 = 0; // 1: holds the prior matrix on chip as bfloat16 (needs the BF16 prior format)
 };
 
 void ls_register_prop_kernels(std::vector<PropKernelInfo>& out);
@@ -59,6 +60,7 @@ struct ls_ctx {
   float* thm = nullptr;           // [L] 1 - mu
   float* thx = nullptr;           // [L] mu
   float* Pi = nullptr;            // [N][N] prior matrix copy (null: uniform)
+  int prior_bf16 = 0;             // LS_PRIOR_BF16: Pi rounded to bfloat16 by ls_set_params
   float pi_u = 0.0f;
   int mu_vec = 0;                 // mu given per locus
   std::vector<double> rho_h, mu_h;  // host copies (the gradient's constant terms)

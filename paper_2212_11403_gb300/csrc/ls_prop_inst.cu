@@ -35,11 +35,11 @@ bool serves_prop(int N) {
 }
 
 // grid = number of targets; CL CTAs (a thread-block cluster when CL = 2) per target
-template <int QS, int CL>
+template <int QS, int CL, int PIM>
 cudaError_t launch_hyb(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s) {
   if (CL == 1) {
-    if (dir == 0) lsk::ls_hyb_kernel<0, QS, 1><<<grid, lsk::kHybThreads, smem, s>>>(p);
-    else lsk::ls_hyb_kernel<1, QS, 1><<<grid, lsk::kHybThreads, smem, s>>>(p);
+    if (dir == 0) lsk::ls_hyb_kernel<0, QS, 1, PIM><<<grid, lsk::kHybThreads, smem, s>>>(p);
+    else lsk::ls_hyb_kernel<1, QS, 1, PIM><<<grid, lsk::kHybThreads, smem, s>>>(p);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -54,31 +54,33 @@ cudaError_t launch_hyb(int dir, const lsk::PropParams& p, int grid, int smem, cu
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (dir == 0) return cudaLaunchKernelEx(&cfg, lsk::ls_hyb_kernel<0, QS, CL>, p);
-  return cudaLaunchKernelEx(&cfg, lsk::ls_hyb_kernel<1, QS, CL>, p);
+  if (dir == 0) return cudaLaunchKernelEx(&cfg, lsk::ls_hyb_kernel<0, QS, CL, PIM>, p);
+  return cudaLaunchKernelEx(&cfg, lsk::ls_hyb_kernel<1, QS, CL, PIM>, p);
 }
-template <int QS>
+template <int QS, int PIM>
 int smem_hyb(int) {
-  return lsk::HybCfg<QS>::smem_bytes();
+  return lsk::HybCfg<QS, PIM>::smem_bytes();
 }
-template <int QS, int CL>
+template <int QS, int CL, int PIM>
 bool serves_hyb(int N) {
-  return lsk::HybCfg<QS>::serves(N, CL);
+  return lsk::HybCfg<QS, PIM>::serves(N, CL);
 }
 
 }  // namespace
 
 // large-N variants: one target per CTA of 16 warps, 12 quads per thread in registers and QS in
 // shared memory
-#define LS_REGH(QS)                                                                                 \
-  out.push_back(PropKernelInfo{1, lsk::kHybThreads / 32, lsk::kHybQR + QS, 0, 0,                    \
-                               {(const void*)lsk::ls_hyb_kernel<0, QS, 1>, (const void*)lsk::ls_hyb_kernel<1, QS, 1>}, \
-                               launch_hyb<QS, 1>, smem_hyb<QS>, serves_hyb<QS, 1>})
+#define LS_REGHX(QS, CL, P)                                                                         \
+  out.push_back(PropKernelInfo{1, lsk::kHybThreads / 32, lsk::kHybQR + QS, P, 0,                    \
+                               {(const void*)lsk::ls_hyb_kernel<0, QS, CL, P>, (const void*)lsk::ls_hyb_kernel<1, QS, CL, P>}, \
+                               launch_hyb<QS, CL, P>, smem_hyb<QS, P>, serves_hyb<QS, CL, P>, CL, P})
+#define LS_REGH(QS) LS_REGHX(QS, 1, 0)
 // a cluster of two CTAs (on two SMs) per target: N in (57344, 2 x 2048 (12 + QS)]
-#define LS_REGH2(QS)                                                                                \
-  out.push_back(PropKernelInfo{1, lsk::kHybThreads / 32, lsk::kHybQR + QS, 0, 0,                    \
-                               {(const void*)lsk::ls_hyb_kernel<0, QS, 2>, (const void*)lsk::ls_hyb_kernel<1, QS, 2>}, \
-                               launch_hyb<QS, 2>, smem_hyb<QS>, serves_hyb<QS, 2>, 2})
+#define LS_REGH2(QS) LS_REGHX(QS, 2, 0)
+// prior matrix, held on chip as bfloat16 (the BF16 prior format): N in (20480, 53248] with one CTA,
+// (53248, 2 x 2048 (12 + QS)] with a cluster of two
+#define LS_REGHP(QS) LS_REGHX(QS, 1, 1)
+#define LS_REGH2P(QS) LS_REGHX(QS, 2, 1)
 
 #define LS_REGP(T, Wp, K, P)                                                                        \
   out.push_back(PropKernelInfo{T, Wp, K, P, 0,                                                      \
@@ -178,6 +180,21 @@ void ls_register_group13(std::vector<PropKernelInfo>& out) {
   LS_REGH(13);
   LS_REGH(14);
   LS_REGH(16);
+}
+#elif LS_INST_GROUP == 14
+void ls_register_group14(std::vector<PropKernelInfo>& out) {
+  // prior matrix (BF16 format), one CTA per target: N in (20480, 53248]
+  LS_REGHP(0);
+  LS_REGHP(4);
+  LS_REGHP(8);
+  LS_REGHP(14);
+}
+#elif LS_INST_GROUP == 15
+void ls_register_group15(std::vector<PropKernelInfo>& out) {
+  // prior matrix (BF16 format), two-CTA clusters: N in (53248, 106496]
+  LS_REGH2P(4);
+  LS_REGH2P(8);
+  LS_REGH2P(14);
 }
 #elif LS_INST_GROUP == 8
 void ls_register_group8(std::vector<PropKernelInfo>& out) {

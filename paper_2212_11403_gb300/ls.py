@@ -35,12 +35,14 @@ LS_FWD = 0
 LS_BWD = 1
 LS_NOALLOC_MAX_N = 65536
 LS_CKPT_F32 = 0
+LS_PRIOR_FP32 = 0
+LS_PRIOR_BF16 = 1
 LS_CKPT_F16 = 1
 LS_MLP_PARAMS = 68353
 
 EXPORTED = [
     "ls_version", "ls_last_error", "ls_create", "ls_create_packed", "ls_destroy", "ls_info", "ls_query",
-    "ls_export_packed", "ls_calc_rho", "ls_set_params", "ls_table_create", "ls_table_destroy", "ls_table_copy",
+    "ls_export_packed", "ls_calc_rho", "ls_set_params", "ls_set_prior_format", "ls_table_create", "ls_table_destroy", "ls_table_copy",
     "ls_table_reset", "ls_table_info", "ls_table_read", "ls_forward", "ls_backward", "ls_posterior", "ls_distance",
     "ls_checkpoints", "ls_ckpt_info", "ls_ckpt_read", "ls_ckpt_replay", "ls_ckpt_destroy",
     "ls_run_all", "ls_run_all_noalloc", "ls_pac_grad", "ls_set_profiling", "ls_profile_read",
@@ -72,6 +74,7 @@ def _load():
         "ls_export_packed": ([P, P], I),
         "ls_calc_rho": ([P, I, D, D, P], I),
         "ls_set_params": ([P, P, P, I, P, P], I),
+        "ls_set_prior_format": ([P, I], I),
         "ls_table_create": ([P, I, I, I, P], I),
         "ls_table_destroy": ([P], I),
         "ls_table_copy": ([P, P, P], I),
@@ -210,6 +213,11 @@ def ls_set_params(ctx, rho, mu, Pi=None):
     h = ctypes.c_uint64()
     _check(_lib.ls_set_params(ctx, rp, mp, mu.size, _dev(Pi, torch.float32, "Pi"), ctypes.byref(h)))
     return h.value
+
+
+def ls_set_prior_format(ctx, fmt):
+    """LS_PRIOR_FP32 or LS_PRIOR_BF16 (applied by the next ls_set_params)."""
+    return _check(_lib.ls_set_prior_format(ctx, int(fmt)))
 
 
 def ls_table_create(ctx, kind, t_from, t_to):

@@ -82,6 +82,39 @@ def measure_prior():
     return out
 
 
+def measure_prior_bf16():
+    """A prior matrix in the BF16 format: the register-tile kernel at N = 20000 (FP32 and BF16
+    formats) and the large-N kernels at N = 50000 (one CTA per target) and N = 100000 (clusters of
+    two), fused fwd + bwd + distance at one decode locus over a short stretch of the cfg3 map
+    (L = 400 for timing; the per-locus cost does not depend on L)."""
+    import torch
+    out = []
+    for N, fmt in ((20000, ls.LS_PRIOR_FP32), (20000, ls.LS_PRIOR_BF16), (50000, ls.LS_PRIOR_BF16),
+                   (100000, ls.LS_PRIOR_BF16)):
+        L = 400
+        w = synth.make_workload("ls_n50000_l20000", N=N, L=L, seed=77 + N, founders=N // 25)
+        loci = np.array([L // 2], dtype=np.int32)
+        Pi = synth.gamma_prior_torch(N + 1, N)
+        ctx = ls.ls_create(w["h"])
+        try:
+            ls.ls_set_prior_format(ctx, fmt)
+            ls.ls_set_params(ctx, w["rho"], w["mu"], Pi)
+            del Pi
+            torch.cuda.empty_cache()
+            d = torch.empty((1, N, N), dtype=torch.float32, device="cuda")
+            t = timed(lambda: ls.ls_run_all(ctx, loci, d, want_pac=False), reps=2)
+            del d
+        finally:
+            ls.ls_destroy(ctx)
+        cells = float(N) * N * L
+        out.append(dict(workload="ls_n50000_l20000 generator with a Gamma(2,1) prior matrix", N=N, L=L, D=1,
+                        prior_format="bf16" if fmt == ls.LS_PRIOR_BF16 else "fp32",
+                        path="dense fwd+bwd+distance, prior matrix", seconds=t, cell_updates_per_s=cells / t,
+                        flop_per_cell=10, frac_fp32=10 * cells / t / P_FP32))
+        torch.cuda.empty_cache()
+    return out
+
+
 def measure_grad():
     import torch
     w = synth.make_workload("ls_n10000_l10000")
@@ -306,7 +339,7 @@ def measure_mlp(n=1 << 25):
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["prior", "grad", "sparse", "sparse_case", "table", "scaling", "mlp"])
+    ap.add_argument("what", choices=["prior", "prior_bf16", "grad", "sparse", "sparse_case", "table", "scaling", "mlp"])
     ap.add_argument("--N", type=int, default=20000, help="sparse_case: haplotypes")
     ap.add_argument("--L", type=int, default=2000, help="sparse_case: loci")
     ap.add_argument("--rows", type=int, default=1 << 25, help="mlp: feature rows")
@@ -317,7 +350,7 @@ def main():
     elif a.what == "mlp":
         recs = measure_mlp(a.rows)
     else:
-        recs = dict(prior=measure_prior, grad=measure_grad, sparse=measure_sparse, table=measure_table,
+        recs = dict(prior=measure_prior, prior_bf16=measure_prior_bf16, grad=measure_grad, sparse=measure_sparse, table=measure_table,
                     scaling=measure_scaling)[a.what]()
     for rec in recs:
         print(json.dumps(rec), flush=True)

@@ -89,6 +89,26 @@ def gamma_prior_f32(seed: int, N: int, chunk: int = 1024) -> np.ndarray:
     return out
 
 
+def gamma_prior_torch(seed: int, N: int, device="cuda", chunk: int = 1024):
+    """float32 [N, N] torch tensor on `device`: the Gamma(2, 1) prior of gamma_prior (each entry the
+    sum of two unit exponentials, diagonal 0, rows normalised in float64), drawn by torch's
+    generator on the device, for N too large for a host matrix.  Rows of it for an oracle are
+    copied back from the tensor."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = torch.empty((N, N), dtype=torch.float32, device=device)
+    for r0 in range(0, N, chunk):
+        r1 = min(N, r0 + chunk)
+        x = torch.empty((r1 - r0, N), dtype=torch.float64, device=device).exponential_(generator=g)
+        x += torch.empty((r1 - r0, N), dtype=torch.float64, device=device).exponential_(generator=g)
+        idx = torch.arange(r0, r1, device=device)
+        x[idx - r0, idx] = 0.0
+        x /= x.sum(dim=1, keepdim=True)
+        out[r0:r1] = x.to(torch.float32)
+    return out
+
+
 def make_workload(name: str, N: int | None = None, L: int | None = None, seed: int | None = None,
                   founders: int | None = None) -> dict:
     """Draw the inputs of a workload (optionally shrunk to N x L for tests).
