@@ -27,7 +27,7 @@ UNITS = [
     ("ls_api.cu", [], "ls_api.o"),
     ("ls_sparse.cu", [], "ls_sparse.o"),
     ("ls_propose.cu", [], "ls_propose.o"),
-] + [("ls_prop_inst.cu", ["-DLS_INST_GROUP=%d" % g], "ls_prop_g%d.o" % g) for g in range(16)]
+] + [("ls_prop_inst.cu", ["-DLS_INST_GROUP=%d" % g], "ls_prop_g%d.o" % g) for g in range(18)]
 
 
 def nvcc() -> str:

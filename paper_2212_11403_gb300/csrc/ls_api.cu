@@ -32,6 +32,8 @@ void ls_register_group12(std::vector<PropKernelInfo>& out);
 void ls_register_group13(std::vector<PropKernelInfo>& out);
 void ls_register_group14(std::vector<PropKernelInfo>& out);
 void ls_register_group15(std::vector<PropKernelInfo>& out);
+void ls_register_group16(std::vector<PropKernelInfo>& out);
+void ls_register_group17(std::vector<PropKernelInfo>& out);
 
 namespace {
 
@@ -73,6 +75,8 @@ std::vector<PropKernelInfo>& registry() {
     ls_register_group13(v);
     ls_register_group14(v);
     ls_register_group15(v);
+    ls_register_group16(v);
+    ls_register_group17(v);
   });
   return v;
 }
@@ -125,8 +129,9 @@ int candidates(ls_ctx* c, Cand* out, int* nout) {
   const bool pin = ov && sscanf(ov, "%d,%d,%d", &pa, &pb, &pk) == 3;
   for (const auto& k : registry()) {
     if (*nout >= kMaxCand) break;
-    if (k.st != 0 || k.pim != pim || !k.serves(N)) continue;
-    if (k.pi16 && !c->prior_bf16) continue;  // holds the prior as bfloat16: only for the BF16 format
+    if (k.st != 0 || (k.pim != 0) != (pim != 0) || !k.serves(N)) continue;
+    // a prior matrix runs on the variants that hold it as bfloat16 exactly when it has the BF16 format
+    if (pim && k.pi16 != c->prior_bf16) continue;
     if (pin && !(k.tpw == pa && k.w == pb && k.kq == pk)) continue;
     const int smem = k.smem_bytes(c->rw2);
     if (smem > 227 * 1024) continue;

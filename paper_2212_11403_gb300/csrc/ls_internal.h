@@ -12,7 +12,7 @@
 // (forward and backward instantiations).
 struct PropKernelInfo {
   int tpw, w, kq;
-  int pim;  // 1: prior-matrix variant
+  int pim;  // prior-matrix variant: 1 FP32 prior values, 2 bfloat16 (0: uniform prior)
   int st;   // 1: statistic-pass variant (launch's dir argument picks ST 1 or ST 2)
   const void* func[2];
   cudaError_t (*launch)(int dir, const lsk::PropParams& p, int grid, int smem, cudaStream_t s);

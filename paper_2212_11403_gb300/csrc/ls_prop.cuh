@@ -217,12 +217,15 @@ struct PropCfg {
   static constexpr int FLAG_OFF = ST_OFF + TPW * 4;
   static constexpr int RING_OFF = ((FLAG_OFF + 16 + 127) / 128) * 128;
   static constexpr int PI_STRIDE = J + 4;  // floats per thread in the prior region (conflict-free 16-B loads)
+  // bfloat16 prior (PIM = 2): halves per thread, rows 8 bytes off a 16-byte multiple (conflict-free
+  // 8-byte loads)
+  static constexpr int PI16_STRIDE = ((J + 7) / 8) * 8 + 4;
   __host__ __device__ static SmemLayout layout(int rw2, int pim) {
     SmemLayout s;
     s.ring_off = RING_OFF;
     s.stg_off = RING_OFF + round_up(kSlots * kRB * rw2 * 4, 128);
     s.pi_off = s.stg_off + THREADS * STG_STRIDE * 4;
-    s.total = s.pi_off + (pim ? THREADS * PI_STRIDE * 4 : 0);
+    s.total = s.pi_off + (pim == 1 ? THREADS * PI_STRIDE * 4 : pim == 2 ? THREADS * PI16_STRIDE * 2 : 0);
     return s;
   }
   // a variant serves N when a slice fits the slots and only a slice's last word is partial
@@ -243,7 +246,9 @@ __host__ __device__ __forceinline__ void slice_of(int sigma, int S, int N, int& 
 
 // PIM = 1: prior matrix.  Each lane keeps its slots' prior values pi_j (zero on padding and on
 // the diagonal) in shared memory; the forward adds rho * pi_j per cell and the backward sums
-// t_j pi_j, so no junk correction is needed.
+// t_j pi_j, so no junk correction is needed.  PIM = 2: the same with the values held as bfloat16
+// (the BF16 prior format, whose values are bfloat16 already, so the conversion is exact): half the
+// shared-memory bytes per cell, two integer operations per pair of cells to widen them.
 //
 // ST > 0 (forward, uniform prior): a second register tile w carries w_j = alpha_j tau_j, tau_j the
 // filtered expectation of an additive statistic S given copying state j.  With S_{l+1} = S_l +
@@ -409,8 +414,10 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   }
   // prior values of this lane's slots (matrix prior): slot s <-> donor (start + s + o) mod N
   const float* pis = reinterpret_cast<const float*>(smem + lay.pi_off) + tid * C::PI_STRIDE;
+  const uint16_t* pis16 = reinterpret_cast<const uint16_t*>(smem + lay.pi_off) + tid * C::PI16_STRIDE;
   if (PIM) {
     float* my = reinterpret_cast<float*>(smem + lay.pi_off) + tid * C::PI_STRIDE;
+    uint16_t* my16 = reinterpret_cast<uint16_t*>(smem + lay.pi_off) + tid * C::PI16_STRIDE;
     int tgt = o + tl;
     tgt = tgt >= N ? tgt - N : tgt;
     const float* prow = p.Pi + (size_t)tgt * N;
@@ -418,7 +425,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       int d = start + s2 + o;
       d = d >= N ? d - N : d;
       d = d >= N ? d - N : d;
-      my[s2] = (s2 < len && d != tgt) ? prow[d] : 0.0f;
+      const float v = (s2 < len && d != tgt) ? prow[d] : 0.0f;
+      if (PIM == 2) my16[s2] = (uint16_t)(__float_as_uint(v) >> 16);  // bfloat16 already: exact
+      else my[s2] = v;
     }
     __syncthreads();
   }
@@ -676,8 +685,16 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
         if (!sel_quad(kn)) th[k % kLA] = load_th(kn);
       }
       if (PIM) {
-        const float4 pv = *reinterpret_cast<const float4*>(pis + 4 * k);
-        const f2 p01 = make_float2(pv.x, pv.y), p23 = make_float2(pv.z, pv.w);
+        f2 p01, p23;
+        if (PIM == 2) {
+          const uint2 pb = *reinterpret_cast<const uint2*>(pis16 + 4 * k);
+          p01 = make_float2(__uint_as_float(pb.x << 16), __uint_as_float(pb.x & 0xffff0000u));
+          p23 = make_float2(__uint_as_float(pb.y << 16), __uint_as_float(pb.y & 0xffff0000u));
+        } else {
+          const float4 pv = *reinterpret_cast<const float4*>(pis + 4 * k);
+          p01 = make_float2(pv.x, pv.y);
+          p23 = make_float2(pv.z, pv.w);
+        }
         if (DIR == 0) {  // u = c x + rho pi_j
           const f2 u01 = __ffma2_rn(C2, x[k][0], __fmul2_rn(R2, p01));
           const f2 u23 = __ffma2_rn(C2, x[k][1], __fmul2_rn(R2, p23));

@@ -86,7 +86,7 @@ bool serves_hyb(int N) {
   out.push_back(PropKernelInfo{T, Wp, K, P, 0,                                                      \
                                {(const void*)lsk::ls_prop_kernel<0, T, Wp, K, P, 0>,                \
                                 (const void*)lsk::ls_prop_kernel<1, T, Wp, K, P, 0>},               \
-                               launch_prop<T, Wp, K, P>, smem_prop<T, Wp, K, P>, serves_prop<T, Wp, K>})
+                               launch_prop<T, Wp, K, P>, smem_prop<T, Wp, K, P>, serves_prop<T, Wp, K>, 1, P == 2})
 #define LS_REG(T, Wp, K) LS_REGP(T, Wp, K, 0)
 // statistic-pass variants: func[0] = ST 1, func[1] = ST 2
 #define LS_REGS(T, Wp, K)                                                                           \
@@ -180,6 +180,21 @@ void ls_register_group13(std::vector<PropKernelInfo>& out) {
   LS_REGH(13);
   LS_REGH(14);
   LS_REGH(16);
+}
+#elif LS_INST_GROUP == 16
+void ls_register_group16(std::vector<PropKernelInfo>& out) {
+  // prior matrix held as bfloat16 (the BF16 prior format), N up to 20480
+  LS_REGP(1, 4, 1, 2);
+  LS_REGP(1, 4, 8, 2);
+  LS_REGP(1, 4, 16, 2);
+  LS_REGP(1, 4, 24, 2);
+}
+#elif LS_INST_GROUP == 17
+void ls_register_group17(std::vector<PropKernelInfo>& out) {
+  LS_REGP(1, 4, 32, 2);
+  LS_REGP(1, 4, 40, 2);
+  LS_REGP(1, 8, 20, 2);
+  LS_REGP(8, 4, 16, 2);
 }
 #elif LS_INST_GROUP == 14
 void ls_register_group14(std::vector<PropKernelInfo>& out) {
