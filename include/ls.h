@@ -147,6 +147,12 @@ int ls_table_info(const ls_table* t, int32_t* kind, int32_t* locus, int32_t* t_f
  * Eq. G, with G = 1 at the last locus).  Either pointer may be NULL.  Enqueued on stream. */
 int ls_table_read(const ls_table* t, float* state, double* logscale, ls_stream_t stream);
 
+/* Sizes the propagation calls (ls_forward, ls_backward, ls_checkpoints, ls_run_all and their
+ * callers) serve: the uniform prior for N up to 114688 (register-tile kernels to N = 20480, one
+ * CTA per target to 57344, two-CTA clusters beyond); a prior matrix up to N = 20480 in either
+ * prior format and up to N = 106496 in the BF16 format.  Beyond these the launch planner returns
+ * LS_ERR_UNSUPPORTED before anything is enqueued. */
+
 /* Forward (Eq. fwd0, fwd1): propagate fwd in place to locus to_locus >= its current locus
  * (an uninitialised table starts at locus 0).  If n_store > 0, alpha at each locus in
  * store_loci (host int32, strictly increasing, within (current, to_locus]) is written to
