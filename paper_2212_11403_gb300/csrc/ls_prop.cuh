@@ -14,11 +14,13 @@
 // is carried to the target locus before moving on).
 //
 // Emission.  Per locus the lane turns its donors' bits into "match" bits (XOR with its target's
-// allele); a 16-entry shared-memory table maps 4 match bits to 4 emission probabilities
-// (theta = 1-mu on a match, mu on a mismatch, App. A.3), one 16-byte load per 4 cells; every other
-// quad of 4 cells instead selects theta by a bit test on the integer pipe, which splits the
-// emission fetch between the shared-memory and integer pipes.  A cell costs three FP32 operations
-// (FFMA, FMUL, FADD as packed f32x2 pairs).
+// allele); a 16-entry shared-memory table maps 4 match bits to 4 emission factors, one 16-byte
+// load per 4 cells; every other quad of 4 cells instead takes them from a bit test (predicates,
+// the integer pipe), which splits the emission fetch between the shared-memory and integer pipes.
+// With the uniform prior theta (1-mu on a match, mu on a mismatch, App. A.3) is b f with
+// b = max(1-mu, mu) folded into the affine step and f in {1, min(1-mu, mu)/b}: the table holds f
+// and the bit-test quads multiply by the ratio under a predicate.  A cell costs three FP32
+// operations (FFMA, FMUL, FADD, mostly as packed f32x2 pairs).
 //
 // Padding and diagonal.  Slots beyond the slice and the diagonal slot are forced to "mismatch".
 // Those junk cells all start at 0 and see the same c, r and theta = mu, so they hold one common

@@ -88,6 +88,29 @@ def test_noalloc_matches_run_all_on_repeated_calls(ls):
             ls.ls_destroy(ctx)
 
 
+@pytest.mark.parametrize("fmt", ["fp32", "bf16"])
+def test_noalloc_matches_run_all_with_a_prior_matrix(ls, fmt):
+    """the prior-matrix variants (FP32 or bfloat16 prior values in shared memory), planned by the
+    same planner: bit-identical distances and status words"""
+    import torch
+    wk = synth.make_workload("ls_n5000_l20000", N=700, L=150, seed=34)
+    N, L, loci = wk["N"], wk["L"], wk["loci"]
+    Pi = torch.from_numpy(synth.gamma_prior_f32(35, N)).cuda()
+    ctx = ls.ls_create(wk["h"])
+    try:
+        if fmt == "bf16":
+            ls.ls_set_prior_format(ctx, ls.LS_PRIOR_BF16)
+        ls.ls_set_params(ctx, wk["rho"], wk["mu"], Pi)
+        rc0, pac0, d0, st0 = reference(ls, ctx, loci, N)
+        rc1, pac1, d1, st1 = noalloc(ls, ctx, loci, N)
+    finally:
+        ls.ls_destroy(ctx)
+    assert rc1 == rc0 == 0
+    np.testing.assert_array_equal(d1, d0)
+    np.testing.assert_array_equal(st1, st0)
+    assert pac_close(pac1, pac0, L, N), (pac1, pac0)
+
+
 def test_noalloc_rejects_n_beyond_its_scratch(ls):
     import torch
     N = ls.LS_NOALLOC_MAX_N + 1
