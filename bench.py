@@ -313,22 +313,30 @@ def main():
     if not args.no_e2e:
         h_pin = torch.from_numpy(np.ascontiguousarray(w["h"])).pin_memory().numpy()
         d_host = torch.empty((D, N, N), dtype=torch.float32, pin_memory=True).numpy()
-        e2e_t = []
+        e2e_t, e2e_ph = [], []
         for s in range(1 + min(args.steps, 3)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            c2 = ls.ls_create(h_pin)
+            c2 = ls.ls_create(h_pin)            # the calls are synchronous: the phase times add up
+            t1 = time.perf_counter()
             ls.ls_set_params(c2, w["rho"], w["mu"])
+            t2 = time.perf_counter()
             ls.ls_run_all(c2, loci, d_host, want_pac=True)
+            t3 = time.perf_counter()
             ls.ls_destroy(c2)
             torch.cuda.synchronize()
+            t4 = time.perf_counter()
             if s > 0:
-                e2e_t.append(time.perf_counter() - t0)
+                e2e_t.append(t4 - t0)
+                e2e_ph.append((t1 - t0, t2 - t1, t3 - t2, t4 - t3))
         te = max_over_ranks(float(np.mean(e2e_t)), world)
+        ph = np.mean(np.array(e2e_ph), axis=0) * 1e3
         h2d = int(w["h"].nbytes + 8 * (L - 1) + 8)
         d2h = int(d_host.nbytes + 8 * N + 4 * N)
         line["e2e"] = {"value": world * cells / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                       "s_per_step": te}
+                       "s_per_step": te,
+                       "phases_ms": {"create (H2D + pack)": float(ph[0]), "set_params": float(ph[1]),
+                                     "run_all (device + D2H of d)": float(ph[2]), "destroy": float(ph[3])}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds, threads=args.cpu_threads)
     ls.ls_destroy(ctx)
