@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   using C = HybCfg<QS, PIM>;
   constexpr int QR = kHybQR, Q = C::Q, B = C::B, NWA = C::NWA, NW = C::NW, T = kHybThreads;
   constexpr int step_dir = DIR == 0 ? 1 : -1;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   float4* Xs = reinterpret_cast<float4*>(smem + C::XS_OFF);    // [QS][T] shared quads
   float4* Stg = reinterpret_cast<float4*>(smem + C::STG_OFF);  // [QR][T] register quads at stores
   uint2* Ps = reinterpret_cast<uint2*>(smem + C::PS_OFF);      // [Q][T] prior quads (PIM)

@@ -34,6 +34,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace lsk {
@@ -557,7 +558,12 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   bool pend_save = false; // forward: save the state after the last step
   const uint32_t* slot_rows = ring;
   int blk_base = 0, blk_n = 0;
-  for (int step = 0; step < p.n_steps; ++step) {
+  // One locus.  EV (a compile-time flag) marks the steps with a store event: a store locus, the
+  // step after it (whose top writes the previous locus' alpha or decode product) and the last step
+  // when the state is saved.  The other steps run a copy of the body without the store branches,
+  // whose register allocation the rare stores then do not constrain.
+  auto body = [&](const int step, auto evc) {
+    constexpr bool EV = decltype(evc)::value;
     const int l = p.l_first + step_dir * step;
     const float cur_omr = nx_omr, cur_rr = nx_rr, cur_thx = nx_thx, cur_thm = nx_thm;
     if (step + 1 < p.n_steps) {
@@ -605,20 +611,20 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
         }
       }
     }
-    const bool is_store = l == next_store_l;
-    const bool save_here = p.save_state && step == p.n_steps - 1;
-    if (DIR == 0 && pend_slot >= 0) {  // alpha of the previous locus
+    const bool is_store = EV && l == next_store_l;
+    const bool save_here = EV && p.save_state && step == p.n_steps - 1;
+    if (EV && DIR == 0 && pend_slot >= 0) {  // alpha of the previous locus
       store_tile(p.store + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f);
       if (ST && p.wstore)
         store_tile(p.wstore + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f, true);
       pend_slot = -1;
     }
 
-    if (DIR == 1 && pend_slot >= 0) {  // decode product of the previous locus: alpha^l t^l, t = theta beta
+    if (EV && DIR == 1 && pend_slot >= 0) {  // decode product of the previous locus: alpha^l t^l, t = theta beta
       store_tile(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
       pend_slot = -1;
     }
-    if (DIR == 1 && ((is_store && p.store) || save_here)) {
+    if (EV && DIR == 1 && ((is_store && p.store) || save_here)) {
       // beta^l = c t^{l+1} + rho, the pre-emission value (tables and stored rows)
       const size_t so = (size_t)(is_store ? p.store_slot[store_next] : 0) * p.state_rows * N;
       store_tile((is_store && p.store) ? p.store + so : nullptr, nullptr, save_here ? p.state : nullptr, true, c, r);
@@ -802,6 +808,18 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     if (lane < TPW && lane % W == warp) lgr[lane * 32 + (step & 31)] = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
     if ((step & 31) == 31 || step == p.n_steps - 1) flush_logs((step & 31) + 1);
     sig_prev = sig;
+  };
+  for (int step = 0; step < p.n_steps;) {
+    // the next event step: now if a store is pending, else the next store locus or the saved last step
+    int ev = p.n_steps;
+    if (pend_slot >= 0) {
+      ev = step;
+    } else {
+      if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
+      if (p.save_state) ev = min(ev, p.n_steps - 1);
+    }
+    for (; step < ev; ++step) body(step, std::false_type{});
+    if (step < p.n_steps) body(step++, std::true_type{});
   }
 
   if (DIR == 1 && pend_slot >= 0)  // decode product of the last locus
