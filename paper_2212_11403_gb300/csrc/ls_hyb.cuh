@@ -271,7 +271,10 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     nthx = p.thx[l];
   };
   load_locus(p.l_first);
-  for (int step = 0; step < p.n_steps; ++step) {
+  // One locus.  EV (compile-time) marks the steps with an event (the first step, a store locus, the
+  // step after it, the last step): the other steps run a copy without those branches.
+  auto body = [&](const int step, auto evc) {
+    constexpr bool EV = decltype(evc)::value;
     const int l = p.l_first + step_dir * step;
     uint32_t cw[NW];
 #pragma unroll
@@ -282,10 +285,10 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     float c, r;
     bool add_log_prev = false;
     const int mi = DIR == 0 ? l - 1 : l;
-    if (step == 0 && p.init) {
+    if (EV && step == 0 && p.init) {
       c = 0.0f;
       r = (DIR == 0 && !PIM) ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
-    } else if (step == 0 && DIR == 1) {
+    } else if (EV && step == 0 && DIR == 1) {
       c = 1.0f;  // backward resume: x = theta^l beta^l from the stored beta
       r = 0.0f;
     } else {
@@ -293,17 +296,17 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
       r = p.rr[mi];
       add_log_prev = DIR == 1;
     }
-    const bool is_store = l == next_store_l;
-    const bool save_here = p.save_state && step == p.n_steps - 1;
-    if (DIR == 0 && pend_slot >= 0) {  // alpha of the previous locus
+    const bool is_store = EV && l == next_store_l;
+    const bool save_here = EV && p.save_state && step == p.n_steps - 1;
+    if (EV && DIR == 0 && pend_slot >= 0) {  // alpha of the previous locus
       store_state(p.store + (size_t)pend_slot * p.state_rows * N, nullptr, nullptr, false, 0.f, 0.f);
       pend_slot = -1;
     }
-    if (DIR == 1 && pend_slot >= 0) {  // decode product of the previous locus: alpha^l t^l, t = theta beta
+    if (EV && DIR == 1 && pend_slot >= 0) {  // decode product of the previous locus: alpha^l t^l, t = theta beta
       store_state(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
       pend_slot = -1;
     }
-    if (DIR == 1 && ((is_store && p.store) || save_here)) {
+    if (EV && DIR == 1 && ((is_store && p.store) || save_here)) {
       // beta^l = c t^{l+1} + rho (tables and stored rows)
       const size_t so = (size_t)(is_store ? p.store_slot[store_next] : 0) * p.state_rows * N;
       store_state((is_store && p.store) ? p.store + so : nullptr, nullptr, save_here ? p.state : nullptr, true, c, r);
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     // Emission as base x f, base = max(1-mu, mu), f in {1, ratio}: a cell is (c base) x + r base,
     // then multiplied by ratio where f = ratio (a predicated multiply, no select).  The "small" bits
     // (f = ratio) are the mismatches, or the matches when mu > 1/2; junk positions have bit 0.
-    if (p.mu_vec || step == 0) {
+    if (p.mu_vec || (EV && step == 0)) {
       u_base = fmaxf(thm, thx);
       u_ratio = u_base > 0.0f ? __fdiv_rn(fminf(thm, thx), u_base) : 0.0f;
     }
@@ -396,6 +399,15 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
       }
     }
     sig_prev = sig;
+  };
+  for (int step = 0; step < p.n_steps;) {
+    // the next event step: the first and the last step, now if a store is pending, else the next
+    // store locus
+    int ev = step == 0 ? 0 : p.n_steps - 1;
+    if (pend_slot >= 0) ev = step;
+    else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
+    for (; step < ev; ++step) body(step, std::false_type{});
+    if (step < p.n_steps) body(step++, std::true_type{});
   }
   if (DIR == 1 && pend_slot >= 0)  // decode product of the last locus
     store_state(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);

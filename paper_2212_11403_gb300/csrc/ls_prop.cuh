@@ -558,10 +558,11 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   bool pend_save = false; // forward: save the state after the last step
   const uint32_t* slot_rows = ring;
   int blk_base = 0, blk_n = 0;
-  // One locus.  EV (a compile-time flag) marks the steps with a store event: a store locus, the
-  // step after it (whose top writes the previous locus' alpha or decode product) and the last step
-  // when the state is saved.  The other steps run a copy of the body without the store branches,
-  // whose register allocation the rare stores then do not constrain.
+  // One locus.  EV (a compile-time flag) marks the steps with an event: the first step, every 32nd
+  // (the log scales are folded) and the last, a store locus, the step after it (whose top writes the
+  // previous locus' alpha or decode product) and the last step when the state is saved.  The other
+  // steps run a copy of the body without those branches, whose register allocation the rare work
+  // then does not constrain.
   auto body = [&](const int step, auto evc) {
     constexpr bool EV = decltype(evc)::value;
     const int l = p.l_first + step_dir * step;
@@ -589,10 +590,10 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     float c, r;
     float cw = 0.0f, rws = 0.0f;  // ST: coefficients of the w recursion
     bool add_log_prev = false;
-    if (step == 0 && p.init) {
+    if (EV && step == 0 && p.init) {
       c = 0.0f;
       r = (DIR == 0 && !PIM) ? p.pi_u : 1.0f;  // alpha^0 = theta pi ; beta^{L-1} = 1
-    } else if (step == 0 && DIR == 1) {
+    } else if (EV && step == 0 && DIR == 1) {
       c = 1.0f;  // backward resume: x = theta^l beta^l from the stored beta
       r = 0.0f;
     } else {
@@ -806,18 +807,15 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     float sig = tot - n_junk * xs;
     if (DIR == 1 && !PIM) sig *= p.pi_u;
     if (lane < TPW && lane % W == warp) lgr[lane * 32 + (step & 31)] = DIR == 0 ? sig : (add_log_prev ? sig_prev : 1.0f);
-    if ((step & 31) == 31 || step == p.n_steps - 1) flush_logs((step & 31) + 1);
+    if (EV && ((step & 31) == 31 || step == p.n_steps - 1)) flush_logs((step & 31) + 1);
     sig_prev = sig;
   };
   for (int step = 0; step < p.n_steps;) {
-    // the next event step: now if a store is pending, else the next store locus or the saved last step
-    int ev = p.n_steps;
-    if (pend_slot >= 0) {
-      ev = step;
-    } else {
-      if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
-      if (p.save_state) ev = min(ev, p.n_steps - 1);
-    }
+    // the next event step: the first step, the next fold of the log scales (every 32nd and the last
+    // step), now if a store is pending, else the next store locus
+    int ev = step == 0 ? 0 : min(step | 31, p.n_steps - 1);
+    if (pend_slot >= 0) ev = step;
+    else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
     for (; step < ev; ++step) body(step, std::false_type{});
     if (step < p.n_steps) body(step++, std::true_type{});
   }
