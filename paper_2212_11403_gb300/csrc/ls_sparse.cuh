@@ -213,19 +213,23 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
     __syncthreads();   // and everyone's
     const float* sc = scal + (t & 1) * kSparseScal * CH;
     bool need_gather = true;
-    for (int jj = 0; jj < nrows; ++jj) {
+    // One locus.  EV (compile-time) marks the event steps: the block's first (the words are
+    // gathered), a window change and a store locus; the other steps run a copy without those
+    // branches.
+    auto body = [&](const int jj, auto evc) {
+      constexpr bool EV = decltype(evc)::value;
       const int kr = DIR == 0 ? jj : nrows - 1 - jj;  // locus l = base + kr is bit kr of the words
       const int l = base + kr;
       const int w = l / p.WS;
       const float tm = sc[0 * CH + kr], tx = sc[1 * CH + kr];
       float c, r;
-      if (cur_w < 0) {  // initial locus: alpha = theta pi ; t = theta (beta = 1)
+      if (EV && cur_w < 0) {  // initial locus: alpha = theta pi ; t = theta (beta = 1)
         enter(w, false, 0.0f);
         need_gather = true;
         c = 0.0f;
         r = DIR == 0 ? pi : 1.0f;
       } else {
-        if (w != cur_w) {
+        if (EV && w != cur_w) {
           const float s_set = set_sum();
           const int nout_old = N - 1 - nset;
           const float fill = (p.pool && nout_old > 0) ? opool / (float)nout_old : 0.0f;
@@ -244,13 +248,13 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
           r = rh;
         }
       }
-      if (need_gather) {
+      if (EV && need_gather) {
         gather(b);
         need_gather = false;
       }
       const uint32_t tb = (twd >> kr) & 1u;
       const uint32_t mk = 1u << kr;
-      const bool is_store = store_next < p.n_store && p.store_loci[store_next] == l;
+      const bool is_store = EV && store_next < p.n_store && p.store_loci[store_next] == l;
       float* srow = is_store ? p.store + ((size_t)p.store_slot[store_next] * N + i) * K : nullptr;
       if (DIR == 1 && is_store) {
         // posterior: alpha (stored by the forward) times beta = c t + r over the set, plus (pool) the
@@ -315,6 +319,20 @@ __global__ void __launch_bounds__(kSparseWarps * 32) ls_sparse_kernel(const Spar
       if (!(tot <= 3.40282347e+38f)) stb |= 2u;  // LS_STATUS_OVERFLOW (infinite or NaN)
       if (DIR == 0) logacc += (double)logf(tot);
       sum_prev = tot;
+    };
+    for (int jj = 0; jj < nrows;) {
+      body(jj++, std::true_type{});
+      // the next event in this block: a window change (the first step whose locus lies outside the
+      // current window) or a store locus
+      int ev = nrows;
+      const int wlo = cur_w * p.WS, whi = wlo + p.WS;  // the current window's loci [wlo, whi)
+      const int lb = DIR == 0 ? whi : wlo - 1;         // the first locus beyond it, in processing order
+      if (lb >= base && lb < base + nrows) ev = min(ev, DIR == 0 ? lb - base : nrows - 1 - (lb - base));
+      if (store_next < p.n_store) {
+        const int ks = p.store_loci[store_next] - base;
+        if (ks >= 0 && ks < nrows) ev = min(ev, DIR == 0 ? ks : nrows - 1 - ks);
+      }
+      for (; jj < ev; ++jj) body(jj, std::false_type{});
     }
   }
   if (active && lane == 0) {
