@@ -564,7 +564,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   // steps run a copy of the body without those branches, whose register allocation the rare work
   // then does not constrain.
   auto body = [&](const int step, auto evc) {
-    constexpr bool EV = decltype(evc)::value;
+    constexpr int KIND = decltype(evc)::value;  // 0 plain, 1 plain opening a ring block (backward), 2 event
+    constexpr bool EV = KIND == 2;
+    constexpr bool RING = DIR == 0 || KIND >= 1;  // the backward's plain steps never open a ring block
     const int l = p.l_first + step_dir * step;
     const float cur_omr = nx_omr, cur_rr = nx_rr, cur_thx = nx_thx, cur_thm = nx_thm;
     if (step + 1 < p.n_steps) {
@@ -578,7 +580,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       }
     }
     const int j = step & (kRB - 1);
-    if (j == 0) {
+    if (RING && j == 0) {
       const int B = step / kRB;
       if (tid == 0 && B >= 1 && B + kSlots - 1 < nblk) issue(B + kSlots - 1);  // slot of block B-1 is free
       mbar_wait_bounded(&bars[B % kSlots], (uint32_t)((B / kSlots) & 1), flag);
@@ -816,8 +818,16 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     int ev = step == 0 ? 0 : min(step | 31, p.n_steps - 1);
     if (pend_slot >= 0) ev = step;
     else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
-    for (; step < ev; ++step) body(step, std::false_type{});
-    if (step < p.n_steps) body(step++, std::true_type{});
+    if (DIR == 0) {
+      for (; step < ev; ++step) body(step, std::integral_constant<int, 0>{});
+    } else {  // the backward measured faster with the ring's block starts in a third copy
+      while (step < ev) {
+        if ((step & (kRB - 1)) == 0) body(step++, std::integral_constant<int, 1>{});
+        const int e2 = min(ev, (step + kRB - 1) & ~(kRB - 1));
+        for (; step < e2; ++step) body(step, std::integral_constant<int, 0>{});
+      }
+    }
+    if (step < p.n_steps) body(step++, std::integral_constant<int, 2>{});
   }
 
   if (DIR == 1 && pend_slot >= 0)  // decode product of the last locus
