@@ -563,7 +563,8 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   // previous locus' alpha or decode product) and the last step when the state is saved.  The other
   // steps run a copy of the body without those branches, whose register allocation the rare work
   // then does not constrain.
-  auto body = [&](const int step, auto evc) {
+  auto body = [&](const int step, auto evc, auto muvc) {
+    constexpr bool MUV = decltype(muvc)::value;
     constexpr int KIND = decltype(evc)::value;  // 0 plain, 1 plain opening a ring block (backward), 2 event
     constexpr bool EV = KIND == 2;
     constexpr bool RING = DIR == 0 || KIND >= 1;  // the backward's plain steps never open a ring block
@@ -574,7 +575,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       const int li = DIR == 0 ? ln - 1 : ln;
       nx_omr = p.omr[li];
       nx_rr = p.rr[li];
-      if (!UNI || p.mu_vec) {  // the emission values change between loci only with a per-locus mu
+      if (!UNI || MUV) {  // the emission values change between loci only with a per-locus mu
         nx_thx = p.thx[ln];
         nx_thm = p.thm[ln];
       }
@@ -636,14 +637,14 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     // ---- the hot loop: FFMA2 + FMUL2 + FADD2 per pair of cells -------------------------------
     uint32_t inv = ((rw[abit >> 5] >> (abit & 31)) & 1u) ? 0u : 0xffffffffu;  // target allele
     // UNI: base, ratio and the sense of the "small" bits of this locus
-    if (UNI && p.mu_vec) {
+    if (UNI && MUV) {
       u_base = fmaxf(cur_thm, cur_thx);
       u_ratio = u_base > 0.0f ? __fdiv_rn(fminf(cur_thm, cur_thx), u_base) : 0.0f;
     }
     if (UNI && cur_thm < cur_thx) inv = ~inv;  // mu > 1/2: the matches carry the smaller factor
     // shared address of this step's table (256-byte aligned, so a byte permute can put a nibble
     // offset in its low byte and the load needs no further address arithmetic)
-    uint32_t lut_b = lut_base + (p.mu_vec ? (uint32_t)((step & 1) << 8) : 0u);
+    uint32_t lut_b = lut_base + (MUV ? (uint32_t)((step & 1) << 8) : 0u);
     // the loads below are plain asm that the compiler may move; deriving their address from a
     // volatile move here keeps them after the previous locus' barrier (which publishes the table)
     asm volatile("mov.b32 %0, %0;" : "+r"(lut_b));
@@ -786,7 +787,7 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     }
 
     // emission table of the next locus (mu varying per locus), into the other buffer
-    if (p.mu_vec && tid < 64 && step + 1 < p.n_steps) {
+    if (MUV && tid < 64 && step + 1 < p.n_steps) {
       const int e = tid >> 2, k = tid & 3;
       if (UNI) {
         const float bs = fmaxf(nx_thm, nx_thx);
@@ -812,23 +813,28 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
     if (EV && ((step & 31) == 31 || step == p.n_steps - 1)) flush_logs((step & 31) + 1);
     sig_prev = sig;
   };
-  for (int step = 0; step < p.n_steps;) {
-    // the next event step: the first step, the next fold of the log scales (every 32nd and the last
-    // step), now if a store is pending, else the next store locus
-    int ev = step == 0 ? 0 : min(step | 31, p.n_steps - 1);
-    if (pend_slot >= 0) ev = step;
-    else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
-    if (DIR == 0) {
-      for (; step < ev; ++step) body(step, std::integral_constant<int, 0>{});
-    } else {  // the backward measured faster with the ring's block starts in a third copy
-      while (step < ev) {
-        if ((step & (kRB - 1)) == 0) body(step++, std::integral_constant<int, 1>{});
-        const int e2 = min(ev, (step + kRB - 1) & ~(kRB - 1));
-        for (; step < e2; ++step) body(step, std::integral_constant<int, 0>{});
+  // the step loop, with the per-locus mu case as a compile-time flag of the step body
+  auto run_steps = [&](auto muvc) {
+    for (int step = 0; step < p.n_steps;) {
+      // the next event step: the first step, the next fold of the log scales (every 32nd and the last
+      // step), now if a store is pending, else the next store locus
+      int ev = step == 0 ? 0 : min(step | 31, p.n_steps - 1);
+      if (pend_slot >= 0) ev = step;
+      else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
+      if (DIR == 0) {
+        for (; step < ev; ++step) body(step, std::integral_constant<int, 0>{}, muvc);
+      } else {  // the backward measured faster with the ring's block starts in a third copy
+        while (step < ev) {
+          if ((step & (kRB - 1)) == 0) body(step++, std::integral_constant<int, 1>{}, muvc);
+          const int e2 = min(ev, (step + kRB - 1) & ~(kRB - 1));
+          for (; step < e2; ++step) body(step, std::integral_constant<int, 0>{}, muvc);
+        }
       }
+      if (step < p.n_steps) body(step++, std::integral_constant<int, 2>{}, muvc);
     }
-    if (step < p.n_steps) body(step++, std::integral_constant<int, 2>{});
-  }
+  };
+  if (p.mu_vec) run_steps(std::true_type{});
+  else run_steps(std::false_type{});
 
   if (DIR == 1 && pend_slot >= 0)  // decode product of the last locus
     store_tile(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
