@@ -262,26 +262,30 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   // loaded one locus ahead
   uint32_t wd[NW], tb;
   float nthm, nthx;
-  auto load_locus = [&](int l) {
+  auto load_locus = [&](int l, bool with_mu) {  // with_mu: also the locus' emission values
     const uint32_t* r = p.bits2 + (size_t)l * p.rw2;
 #pragma unroll
     for (int k = 0; k < NW; ++k) wd[k] = (w0 + k < p.rw2) ? r[w0 + k] : 0u;
     tb = (r[tgt >> 5] >> (tgt & 31)) & 1u;
-    nthm = p.thm[l];
-    nthx = p.thx[l];
+    if (with_mu) {
+      nthm = p.thm[l];
+      nthx = p.thx[l];
+    }
   };
-  load_locus(p.l_first);
+  load_locus(p.l_first, true);
   // One locus.  EV (compile-time) marks the steps with an event (the first step, a store locus, the
-  // step after it, the last step): the other steps run a copy without those branches.
-  auto body = [&](const int step, auto evc) {
+  // step after it, the last step): the other steps run a copy without those branches.  MUV
+  // (compile-time): mu varies per locus (otherwise the first locus' emission values serve all).
+  auto body = [&](const int step, auto evc, auto muvc) {
     constexpr bool EV = decltype(evc)::value;
+    constexpr bool MUV = decltype(muvc)::value;
     const int l = p.l_first + step_dir * step;
     uint32_t cw[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) cw[k] = wd[k];
     const uint32_t ctb = tb;
     const float thm = nthm, thx = nthx;
-    if (step + 1 < p.n_steps) load_locus(l + step_dir);
+    if (step + 1 < p.n_steps) load_locus(l + step_dir, MUV);
     float c, r;
     bool add_log_prev = false;
     const int mi = DIR == 0 ? l - 1 : l;
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     // Emission as base x f, base = max(1-mu, mu), f in {1, ratio}: a cell is (c base) x + r base,
     // then multiplied by ratio where f = ratio (a predicated multiply, no select).  The "small" bits
     // (f = ratio) are the mismatches, or the matches when mu > 1/2; junk positions have bit 0.
-    if (p.mu_vec || (EV && step == 0)) {
+    if (MUV || (EV && step == 0)) {
       u_base = fmaxf(thm, thx);
       u_ratio = u_base > 0.0f ? __fdiv_rn(fminf(thm, thx), u_base) : 0.0f;
     }
@@ -400,15 +404,19 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     }
     sig_prev = sig;
   };
-  for (int step = 0; step < p.n_steps;) {
-    // the next event step: the first and the last step, now if a store is pending, else the next
-    // store locus
-    int ev = step == 0 ? 0 : p.n_steps - 1;
-    if (pend_slot >= 0) ev = step;
-    else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
-    for (; step < ev; ++step) body(step, std::false_type{});
-    if (step < p.n_steps) body(step++, std::true_type{});
-  }
+  auto run_steps = [&](auto muvc) {
+    for (int step = 0; step < p.n_steps;) {
+      // the next event step: the first and the last step, now if a store is pending, else the next
+      // store locus
+      int ev = step == 0 ? 0 : p.n_steps - 1;
+      if (pend_slot >= 0) ev = step;
+      else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
+      for (; step < ev; ++step) body(step, std::false_type{}, muvc);
+      if (step < p.n_steps) body(step++, std::true_type{}, muvc);
+    }
+  };
+  if (p.mu_vec) run_steps(std::true_type{});
+  else run_steps(std::false_type{});
   if (DIR == 1 && pend_slot >= 0)  // decode product of the last locus
     store_state(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
   if (DIR == 0 && (pend_slot >= 0 || pend_save))

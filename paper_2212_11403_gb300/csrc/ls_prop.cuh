@@ -565,12 +565,13 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   // then does not constrain.
   auto body = [&](const int step, auto evc, auto muvc) {
     constexpr bool MUV = decltype(muvc)::value;
-    constexpr int KIND = decltype(evc)::value;  // 0 plain, 1 plain opening a ring block (backward), 2 event
+    constexpr int KIND = decltype(evc)::value;  // 0 plain, 1 plain opening a ring block, 2 event
     constexpr bool EV = KIND == 2;
-    constexpr bool RING = DIR == 0 || KIND >= 1;  // the backward's plain steps never open a ring block
+    constexpr bool RING = KIND >= 1;  // plain steps never open a ring block
     const int l = p.l_first + step_dir * step;
     const float cur_omr = nx_omr, cur_rr = nx_rr, cur_thx = nx_thx, cur_thm = nx_thm;
-    if (step + 1 < p.n_steps) {
+    // (a plain step is never the last; the forward measured faster without the test there)
+    if ((DIR == 0 && !EV) || step + 1 < p.n_steps) {
       const int ln = l + step_dir;
       const int li = DIR == 0 ? ln - 1 : ln;
       nx_omr = p.omr[li];
@@ -821,14 +822,11 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       int ev = step == 0 ? 0 : min(step | 31, p.n_steps - 1);
       if (pend_slot >= 0) ev = step;
       else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
-      if (DIR == 0) {
-        for (; step < ev; ++step) body(step, std::integral_constant<int, 0>{}, muvc);
-      } else {  // the backward measured faster with the ring's block starts in a third copy
-        while (step < ev) {
-          if ((step & (kRB - 1)) == 0) body(step++, std::integral_constant<int, 1>{}, muvc);
-          const int e2 = min(ev, (step + kRB - 1) & ~(kRB - 1));
-          for (; step < e2; ++step) body(step, std::integral_constant<int, 0>{}, muvc);
-        }
+      // the steps that open a TMA ring block (every kRB-th) run in their own copy
+      while (step < ev) {
+        if ((step & (kRB - 1)) == 0) body(step++, std::integral_constant<int, 1>{}, muvc);
+        const int e2 = min(ev, (step + kRB - 1) & ~(kRB - 1));
+        for (; step < e2; ++step) body(step, std::integral_constant<int, 0>{}, muvc);
       }
       if (step < p.n_steps) body(step++, std::integral_constant<int, 2>{}, muvc);
     }
