@@ -331,12 +331,20 @@ def main():
                 e2e_ph.append((t1 - t0, t2 - t1, t3 - t2, t4 - t3))
         te = max_over_ranks(float(np.mean(e2e_t)), world)
         ph = np.mean(np.array(e2e_ph), axis=0) * 1e3
+        # the host link on this machine: one pinned device-to-host copy of d's size (outside the timed region)
+        d_host_t = torch.from_numpy(d_host)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_host_t.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        d2h_gbs = d.numel() * 4 / (time.perf_counter() - t0) / 1e9
         h2d = int(w["h"].nbytes + 8 * (L - 1) + 8)
         d2h = int(d_host.nbytes + 8 * N + 4 * N)
         line["e2e"] = {"value": world * cells / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "s_per_step": te,
                        "phases_ms": {"create (H2D + pack)": float(ph[0]), "set_params": float(ph[1]),
-                                     "run_all (device + D2H of d)": float(ph[2]), "destroy": float(ph[3])}}
+                                     "run_all (device + D2H of d)": float(ph[2]), "destroy": float(ph[3])},
+                       "d2h_gbs_of_this_host": d2h_gbs}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds, threads=args.cpu_threads)
     ls.ls_destroy(ctx)
