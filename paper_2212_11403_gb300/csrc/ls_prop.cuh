@@ -558,16 +558,23 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   bool pend_save = false; // forward: save the state after the last step
   const uint32_t* slot_rows = ring;
   int blk_base = 0, blk_n = 0;
+  // The steps that open a TMA ring block get their own copy of the step body, except in the
+  // backward of the widest one-target-per-CTA tiles, where a third copy of the body spilled
+  // registers.
+  constexpr bool kRingCopy = !(TPW == 1 && DIR == 1 && KQ >= 32);
   // One locus.  EV (a compile-time flag) marks the steps with an event: the first step, every 32nd
   // (the log scales are folded) and the last, a store locus, the step after it (whose top writes the
   // previous locus' alpha or decode product) and the last step when the state is saved.  The other
   // steps run a copy of the body without those branches, whose register allocation the rare work
   // then does not constrain.
   auto body = [&](const int step, auto evc, auto muvc) {
-    constexpr bool MUV = decltype(muvc)::value;
+    // per-locus mu: 0 no, 1 yes (compile-time), 2 decided at run time (the FP32 prior-matrix
+    // variants, whose larger body spilled when compiled twice)
+    constexpr int MUVK = decltype(muvc)::value;
+    const bool MUV = MUVK == 2 ? p.mu_vec != 0 : MUVK == 1;
     constexpr int KIND = decltype(evc)::value;  // 0 plain, 1 plain opening a ring block, 2 event
     constexpr bool EV = KIND == 2;
-    constexpr bool RING = KIND >= 1;  // plain steps never open a ring block
+    constexpr bool RING = KIND >= 1 || !kRingCopy;  // plain steps never open a ring block
     const int l = p.l_first + step_dir * step;
     const float cur_omr = nx_omr, cur_rr = nx_rr, cur_thx = nx_thx, cur_thm = nx_thm;
     // (a plain step is never the last; the forward measured faster without the test there)
@@ -823,6 +830,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       if (pend_slot >= 0) ev = step;
       else if (next_store_l >= 0) ev = min(ev, (next_store_l - p.l_first) * step_dir);
       // the steps that open a TMA ring block (every kRB-th) run in their own copy
+      if (!kRingCopy) {
+        for (; step < ev; ++step) body(step, std::integral_constant<int, 0>{}, muvc);
+      }
       while (step < ev) {
         if ((step & (kRB - 1)) == 0) body(step++, std::integral_constant<int, 1>{}, muvc);
         const int e2 = min(ev, (step + kRB - 1) & ~(kRB - 1));
@@ -831,8 +841,9 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
       if (step < p.n_steps) body(step++, std::integral_constant<int, 2>{}, muvc);
     }
   };
-  if (p.mu_vec) run_steps(std::true_type{});
-  else run_steps(std::false_type{});
+  if (PIM == 1) run_steps(std::integral_constant<int, 2>{});
+  else if (p.mu_vec) run_steps(std::integral_constant<int, 1>{});
+  else run_steps(std::integral_constant<int, 0>{});
 
   if (DIR == 1 && pend_slot >= 0)  // decode product of the last locus
     store_tile(nullptr, p.alpha_dec + (size_t)pend_slot * p.state_rows * N, nullptr, false, 0.f, 0.f);
