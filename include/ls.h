@@ -291,6 +291,15 @@ int ls_mlp_train(ls_mlp* m, const float* X, const float* y, int64_t n, int32_t s
  * Synchronous. */
 int ls_propose_window(ls_ctx* ctx, int32_t C, int32_t w, int32_t* cand_out, float* feat_out, ls_stream_t stream);
 
+/* Training labels of the learned proposal (no counterpart in the paper): for the stage-1 candidates
+ * cand (device int32 [N][C], as ls_propose_window writes them) and the dense posteriors P (device
+ * float [N][N], row i the posterior of target i over donors at the window's middle locus, as
+ * ls_posterior_rows writes them), y_out (device float [N][C]) receives
+ * y = 1 + log10(max(p, 1e-12)) / 12 (1 for p = 1, 0 at 1e-12 and below), the network's regression
+ * target; 0 where cand is -1 (padding) and NaN where an id is >= N.  N is the context's.
+ * Synchronous. */
+int ls_propose_labels(ls_ctx* ctx, const float* P, const int32_t* cand, int32_t C, float* y_out, ls_stream_t stream);
+
 /* Donor sets for every window: idx_out device int32 [N][ceil(L/256)][K] in ascending id order.
  * With mlp NULL the K donors are stage 1's (C ignored); otherwise stage 1 keeps C (K <= C <= 2048)
  * and the network keeps the K best scores (ties to the lower id).  1 <= K <= 512.  Synchronous. */

@@ -14,7 +14,9 @@ chain's paths (tests/test_oracle_proposal.py):
   * the features of a candidate are the match fractions 1 - count / n of windows w-3..w+3, window
     indices clamped to [0, Wn-1], then one zero;
   * the network maps 8 inputs through 256 and 256 ReLU units to one score; the loss is half the
-    mean squared error.
+    mean squared error;
+  * the training label of a candidate is its dense posterior on a log scale,
+    y = 1 + log10(max(p, 1e-12)) / 12 (pinned by its closed-form values).
 """
 from __future__ import annotations
 
@@ -119,6 +121,19 @@ def mlp_loss_grad(p, X, y):
     g[P_W1:P_B1] = (X.T @ dZ1).reshape(-1)
     g[P_B1:P_W2] = dZ1.sum(axis=0)
     return loss, g
+
+
+def labels(P, cand):
+    """y [N, C]: 1 + log10(max(P[i, cand[i, c]], 1e-12)) / 12 for a candidate, 0 for padding (-1)."""
+    P = np.asarray(P, dtype=np.float64)
+    cand = np.asarray(cand)
+    y = np.zeros(cand.shape)
+    for i in range(cand.shape[0]):
+        for c in range(cand.shape[1]):
+            j = int(cand[i, c])
+            if j >= 0:
+                y[i, c] = 1.0 + np.log10(max(P[i, j], 1e-12)) / 12.0
+    return y
 
 
 def lookahead_sets(S, span=1):

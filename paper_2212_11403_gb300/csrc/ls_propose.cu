@@ -380,6 +380,16 @@ int ls_propose_window(ls_ctx* ctx, int32_t C, int32_t w, int32_t* cand_out, floa
   return LS_OK;
 }
 
+int ls_propose_labels(ls_ctx* ctx, const float* P, const int32_t* cand, int32_t C, float* y_out, ls_stream_t stream) {
+  if (!ctx || !P || !cand || !y_out || C < 1) return fail(LS_ERR_ARG, "bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  lsk::label_kernel<<<8 * ctx->num_sms, 256, 0, s>>>(P, cand, ctx->N, C, 1e-12f, y_out);
+  TRY(cudaGetLastError());
+  TRY(cudaStreamSynchronize(s));
+  return LS_OK;
+}
+
 int ls_propose(ls_ctx* ctx, int32_t C, int32_t K, const ls_mlp* mlp, int32_t* idx_out, ls_stream_t stream) {
   if (!ctx || K < 1 || K > 512 || !idx_out) return fail(LS_ERR_ARG, "bad arguments (1 <= K <= 512)");
   if (mlp && (C < K || C > 2048)) return fail(LS_ERR_ARG, "need K <= C <= 2048 candidates for the MLP stage");

@@ -270,4 +270,19 @@ __global__ void topk_kernel(const int32_t* __restrict__ cand, const float* __res
   for (int q = threadIdx.x; q < K; q += blockDim.x) idx[((size_t)i * Wn + w) * K + q] = val[q];
 }
 
+// Training labels of the stage-1 candidates of one window, one thread per (target, candidate):
+// y = 1 + log10(max(p_ij, floor)) / 12 with p_ij the dense posterior of candidate j for target i
+// (row-major P [N][N]); 0 for padding (-1) and NaN for an id outside [0, N).
+__global__ void label_kernel(const float* __restrict__ P, const int32_t* __restrict__ cand, int N, int C, float floor,
+                             float* __restrict__ y) {
+  const long long n = (long long)N * C;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int j = cand[e];
+    float v = 0.0f;
+    if (j >= N) v = __int_as_float(0x7fc00000);
+    else if (j >= 0) v = 1.0f + log10f(fmaxf(P[(size_t)(e / C) * N + j], floor)) * (1.0f / 12.0f);
+    y[e] = v;
+  }
+}
+
 }  // namespace lsk

@@ -47,7 +47,7 @@ EXPORTED = [
     "ls_checkpoints", "ls_ckpt_info", "ls_ckpt_read", "ls_ckpt_replay", "ls_ckpt_destroy",
     "ls_run_all", "ls_run_all_noalloc", "ls_pac_grad", "ls_set_profiling", "ls_profile_read",
     "ls_posterior_rows", "ls_mlp_create", "ls_mlp_destroy", "ls_mlp_get", "ls_mlp_set", "ls_mlp_forward",
-    "ls_mlp_grad", "ls_mlp_train", "ls_propose_window", "ls_propose", "ls_sparse_run_all",
+    "ls_mlp_grad", "ls_mlp_train", "ls_propose_window", "ls_propose_labels", "ls_propose", "ls_sparse_run_all",
 ]
 
 
@@ -102,6 +102,7 @@ def _load():
         "ls_mlp_grad": ([P, P, P, I, P, P, P], I),
         "ls_mlp_train": ([P, P, P, ctypes.c_int64, I, I, ctypes.c_float, ctypes.c_uint64, P, P], I),
         "ls_propose_window": ([P, I, I, P, P, P], I),
+        "ls_propose_labels": ([P, P, P, I, P, P], I),
         "ls_propose": ([P, I, I, P, P, P], I),
         "ls_sparse_run_all": ([P, P, I, I, I, I, P, I, P, ctypes.c_float, P, P, P, P, ctypes.c_float, P, P, P], I),
         "ls_set_profiling": ([P, I], I),
@@ -413,6 +414,12 @@ def ls_propose_window(ctx, C, w, cand_out, feat_out=None, stream=None):
     import torch
     return _check(_lib.ls_propose_window(ctx, int(C), int(w), _dev(cand_out, torch.int32, "cand_out"),
                                          _dev(feat_out, torch.float32, "feat_out"), _stream(stream)))
+
+
+def ls_propose_labels(ctx, P, cand, C, y_out, stream=None):
+    import torch
+    return _check(_lib.ls_propose_labels(ctx, _dev(P, torch.float32, "P"), _dev(cand, torch.int32, "cand"), int(C),
+                                         _dev(y_out, torch.float32, "y_out"), _stream(stream)))
 
 
 def ls_propose(ctx, C, K, mlp, idx_out, stream=None):

@@ -4,8 +4,8 @@ library's MLP kernels, and the proposal / sparse pipeline.
 Labels.  For target i, window w and stage-1 candidate j the label is the dense posterior p_ij at
 the window's middle locus on a log scale, y = 1 + log10(max(p, 1e-12)) / 12 (1 for p = 1, 0 at
 1e-12 and below), so the network ranks candidates by predicted posterior mass.  The posteriors,
-the features and every step of training run in libls; this module moves tensors between the
-calls (gathering labels at candidate indices, dropping padded candidates).
+the features, the labels and every step of training run in libls; this module moves tensors
+between the calls (dropping padded candidates).
 """
 from __future__ import annotations
 
@@ -14,7 +14,6 @@ import numpy as np
 from . import ls
 
 WS = 256
-P_FLOOR = 1e-12
 
 
 def window_mid(L: int, w: int) -> int:
@@ -44,11 +43,6 @@ def dense_posteriors(ctx, N: int, loci):
     return P
 
 
-def labels(p):
-    import torch
-    return 1.0 + torch.log10(torch.clamp(p, min=P_FLOOR)) / 12.0
-
-
 def training_set(ctx, N: int, L: int, C: int, wins, P=None):
     """(X [n, 8], y [n]) CUDA float32 over the stage-1 candidates of the windows `wins`; P are the
     dense posteriors at their middle loci (computed when None)."""
@@ -58,12 +52,13 @@ def training_set(ctx, N: int, L: int, C: int, wins, P=None):
     Xs, ys = [], []
     cand = torch.empty((N, C), dtype=torch.int32, device="cuda")
     feat = torch.empty((N, C, 8), dtype=torch.float32, device="cuda")
+    yw = torch.empty((N, C), dtype=torch.float32, device="cuda")
     for k, w in enumerate(wins):
         ls.ls_propose_window(ctx, C, int(w), cand, feat)
+        ls.ls_propose_labels(ctx, P[k], cand, C, yw)
         valid = cand >= 0
-        pc = torch.gather(P[k], 1, cand.clamp(min=0).long())
         Xs.append(feat[valid])
-        ys.append(labels(pc)[valid])
+        ys.append(yw[valid])
     return torch.cat(Xs).contiguous(), torch.cat(ys).contiguous()
 
 

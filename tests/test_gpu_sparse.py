@@ -95,6 +95,33 @@ def test_raw_proposal_and_features_match_oracle(ls):
         assert float(np.max(np.abs(gf - rf))) <= 1e-6
 
 
+def test_training_labels_match_oracle(ls):
+    # posteriors from 1e-16 to 1 (and exact zeros) at random candidates, -1 padding and one id
+    # outside [0, N) (NaN by the header's contract)
+    import torch
+    rng = np.random.default_rng(31)
+    w = synth.make_workload("ls_n50000_l20000", N=150, L=300, seed=22)
+    N, C = w["N"], 64
+    P = np.exp(rng.uniform(np.log(1e-16), 0.0, size=(N, N))).astype(np.float32)
+    P[rng.random((N, N)) < 0.05] = 0.0
+    P[0, 0] = 1.0
+    cand = rng.integers(-1, N, size=(N, C)).astype(np.int32)
+    cand[0, 0] = 0
+    cand[1, 3] = N
+    ctx = ls.ls_create(w["h"])
+    try:
+        y = torch.full((N, C), -7.0, dtype=torch.float32, device="cuda")
+        ls.ls_propose_labels(ctx, torch.from_numpy(P).cuda(), torch.from_numpy(cand).cuda(), C, y)
+        y = y.cpu().numpy()
+    finally:
+        ls.ls_destroy(ctx)
+    assert np.isnan(y[1, 3]) and y[0, 0] == 1.0
+    cand[1, 3] = -1
+    y[1, 3] = 0.0
+    ref = op.labels(P.astype(np.float64), cand)
+    assert float(np.max(np.abs(y - ref))) <= 3e-6
+
+
 def test_mlp_inference_and_gradient_match_oracle(ls):
     import torch
     rng = np.random.default_rng(5)

@@ -58,6 +58,15 @@ def test_stage1_pads_when_fewer_donors_than_c():
     assert np.all(cand[:, 3:] == -1) and np.all(cand[:, :3] >= 0)
 
 
+def test_labels_closed_form_values():
+    # p = 1 -> 1, p = 1e-6 -> 1/2, p = 1e-12 and below (0 too) -> 0, padding -> 0; the row of
+    # each candidate is its own target's
+    P = np.array([[1.0, 1e-6, 1e-12], [0.0, 1e-3, 1e-15]])
+    cand = np.array([[0, 1, 2, -1], [0, 1, 2, -1]])
+    y = op.labels(P, cand)
+    np.testing.assert_allclose(y, [[1.0, 0.5, 0.0, 0.0], [0.0, 0.75, 0.0, 0.0]], rtol=0, atol=1e-15)
+
+
 def test_mlp_gradient_matches_finite_differences():
     rng = np.random.default_rng(4)
     p = rng.normal(0, 0.2, op.N_PARAMS)
