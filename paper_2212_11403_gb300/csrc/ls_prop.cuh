@@ -314,31 +314,84 @@ __global__ void __launch_bounds__(W * 32, ((PIM || ST) && W >= 8) ? 1 : 2) ls_pr
   // ---- staged transfers between the register tile and global memory (store loci only) ------
   // element (src thread, slot s of chunk c) <-> donor (start_src + 32c + s + o) mod N of target
   // o + tl_src; consecutive threads take consecutive slots, so global accesses are contiguous.
-  // to global: w1 = v, m1 *= v, w2 = v (any may be null); from global: gbase into the staging chunk
+  // to global: w1 = v, m1 *= v, w2 = v (any may be null); from global: gbase into the staging chunk.
+  // The backward of the tiles with up to 255 registers a thread takes a thread's elements in batches
+  // of kXB and issues a batch's loads before its stores (the compiler cannot tell the stores from
+  // later loads, so the read-modify-write of the decode products would otherwise wait one memory
+  // latency per element); the forward, which only reads when it resumes from a table, and the
+  // 8-warp tiles (128 registers) keep one element at a time (measured faster, and no spills).
   auto xfer = [&](int c, float* gbase, float* w1, float* m1, float* w2, bool to_global) {
-    for (int idx = tid; idx < THREADS * 32; idx += THREADS) {
-      const int src = idx >> 5, s = idx & 31;
-      const int ln = src & 31;
-      const int t_s = ln % TPW, sg = (src >> 5) * SPW + ln / TPW;
-      int st, ln_s;
-      slice_of(sg, S, N, st, ln_s);
-      const int gs = 32 * c + s;
-      float* sp = stg + src * C::STG_STRIDE + s;
-      const bool diag = sg == 0 && gs == t_s;
-      const bool ok = gs < ln_s && cta_t + t_s < t_end;
-      int d = st + gs + o;
-      d = d >= N ? d - N : d;
-      d = d >= N ? d - N : d;
-      const size_t ro = (size_t)(row0 + t_s) * N + d;
-      if (to_global) {
-        if (ok) {
-          const float v = diag ? 0.0f : *sp;
-          if (w1) w1[ro] = v;
-          if (m1) m1[ro] = diag ? 0.0f : m1[ro] * (v * kProdScale);
-          if (w2) w2[ro] = v;
+    if constexpr (DIR == 0 || W >= 8) {
+      for (int idx = tid; idx < THREADS * 32; idx += THREADS) {
+        const int src = idx >> 5, s = idx & 31;
+        const int ln = src & 31;
+        const int t_s = ln % TPW, sg = (src >> 5) * SPW + ln / TPW;
+        int st, ln_s;
+        slice_of(sg, S, N, st, ln_s);
+        const int gs = 32 * c + s;
+        float* sp = stg + src * C::STG_STRIDE + s;
+        const bool diag = sg == 0 && gs == t_s;
+        const bool ok = gs < ln_s && cta_t + t_s < t_end;
+        int d = st + gs + o;
+        d = d >= N ? d - N : d;
+        d = d >= N ? d - N : d;
+        const size_t ro = (size_t)(row0 + t_s) * N + d;
+        if (to_global) {
+          if (ok) {
+            const float v = diag ? 0.0f : *sp;
+            if (w1) w1[ro] = v;
+            if (m1) m1[ro] = diag ? 0.0f : m1[ro] * (v * kProdScale);
+            if (w2) w2[ro] = v;
+          }
+        } else {
+          *sp = (ok && !diag) ? gbase[ro] : 0.0f;
         }
-      } else {
-        *sp = (ok && !diag) ? gbase[ro] : 0.0f;
+      }
+      return;
+    }
+    constexpr int kXB = 8;
+    for (int i0 = tid; i0 < THREADS * 32; i0 += THREADS * kXB) {
+      size_t ro[kXB];
+      bool ok[kXB], dg[kXB];
+      float gv[kXB];
+#pragma unroll
+      for (int b = 0; b < kXB; ++b) {
+        const int idx = i0 + b * THREADS;
+        const int src = idx >> 5, s = idx & 31;
+        const int ln = src & 31;
+        const int t_s = ln % TPW, sg = (src >> 5) * SPW + ln / TPW;
+        int st, ln_s;
+        slice_of(sg, S, N, st, ln_s);
+        const int gs = 32 * c + s;
+        dg[b] = sg == 0 && gs == t_s;
+        ok[b] = gs < ln_s && cta_t + t_s < t_end;
+        int d = st + gs + o;
+        d = d >= N ? d - N : d;
+        d = d >= N ? d - N : d;
+        ro[b] = (size_t)(row0 + t_s) * N + d;
+      }
+#pragma unroll
+      for (int b = 0; b < kXB; ++b) {
+        gv[b] = 0.0f;
+        if (ok[b] && !dg[b]) {
+          if (!to_global) gv[b] = gbase[ro[b]];
+          else if (m1) gv[b] = m1[ro[b]];
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kXB; ++b) {
+        const int idx = i0 + b * THREADS;
+        float* sp = stg + (idx >> 5) * C::STG_STRIDE + (idx & 31);
+        if (to_global) {
+          if (ok[b]) {
+            const float v = dg[b] ? 0.0f : *sp;
+            if (w1) w1[ro[b]] = v;
+            if (m1) m1[ro[b]] = dg[b] ? 0.0f : gv[b] * (v * kProdScale);
+            if (w2) w2[ro[b]] = v;
+          }
+        } else {
+          *sp = gv[b];
+        }
       }
     }
   };
