@@ -195,6 +195,28 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
   };
   // store the row (x, or c x + r when affine) to w1 / multiply m1 by it / w2 (any may be null)
   auto store_state = [&](float* w1, float* m1, float* w2, bool affine, float c, float r) {
+    if (PIM && m1 && !w1 && !w2) {  // decode products: a quad's four loads ahead of its stores
+      auto put4 = [&](int pos, float x0, float x1, float x2, float x3) {
+        const float xv[4] = {x0, x1, x2, x3};
+        float gv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          gv[e] = (pos + e < N && pos + e != tgt) ? m1[(size_t)row * N + pos + e] : 0.0f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (pos + e < N) {
+            const float v = pos + e == tgt ? 0.0f : (affine ? fmaf(c, xv[e], r) : xv[e]);
+            m1[(size_t)row * N + pos + e] = pos + e == tgt ? 0.0f : gv[e] * (v * kProdScale);
+          }
+      };
+#pragma unroll
+      for (int q = 0; q < QR; ++q) put4(d0 + 4 * q, x[q][0].x, x[q][0].y, x[q][1].x, x[q][1].y);
+      for (int q = QR; q < Q; ++q) {
+        const float4 v = Xs[(q - QR) * T + tid];
+        put4(d0 + 4 * q, v.x, v.y, v.z, v.w);
+      }
+      return;
+    }
     if (PIM) {  // every thread writes its own positions
       auto put = [&](int pos, float xv) {
         if (pos >= N) return;
@@ -224,6 +246,32 @@ __global__ void __launch_bounds__(kHybThreads, 1) ls_hyb_kernel(const PropParams
     for (int q = 0; q < QR; ++q) Stg[q * T + tid] = make_float4(x[q][0].x, x[q][0].y, x[q][1].x, x[q][1].y);
     __syncthreads();
     const int iend = min(C::NP, N - pos0);
+    if (m1 && !w1 && !w2) {
+      // decode products: a thread's loads of kXB elements go out ahead of their stores (the
+      // compiler cannot tell a store from later loads, so each load would otherwise wait for the
+      // previous element's store)
+      constexpr int kXB = 8;
+      for (int i0 = tid; i0 < iend; i0 += T * kXB) {
+        float gv[kXB];
+#pragma unroll
+        for (int b = 0; b < kXB; ++b) {
+          const int i = i0 + b * T, g = pos0 + i;
+          gv[b] = (i < iend && g != tgt) ? m1[(size_t)row * N + g] : 0.0f;
+        }
+#pragma unroll
+        for (int b = 0; b < kXB; ++b) {
+          const int i = i0 + b * T;
+          if (i < iend) {
+            const int t = i / B, o = i - t * B, g = pos0 + i;
+            const float xv = *elem(o >> 2, t, o & 3);
+            const float v = g == tgt ? 0.0f : (affine ? fmaf(c, xv, r) : xv);
+            m1[(size_t)row * N + g] = g == tgt ? 0.0f : gv[b] * (v * kProdScale);
+          }
+        }
+      }
+      __syncthreads();
+      return;
+    }
     for (int i = tid; i < iend; i += T) {
       const int t = i / B, o = i - t * B, g = pos0 + i;
       const float xv = *elem(o >> 2, t, o & 3);
