@@ -58,3 +58,22 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
                               cpu_threads=1)
     assert bench.run_reference(args, 2, 1) is None   # another rank: no work, no output
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(capsys):
+    # the oracle arm's JSON line on a small instance: the contract's keys, the oracle as the
+    # baseline, no host-device copies
+    import argparse
+
+    import bench
+    args = argparse.Namespace(workload="ls_n200_l1000", N=60, L=80, steps=1, warmup=0, cpu_seconds=1.0,
+                              cpu_threads=1)
+    bench.run_reference(args, 1, 0)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["n_gpus"] == 1
+    assert line["config"]["N"] == 60 and line["config"]["L"] == 80
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] == 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
